@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Decompression benchmark (decompressed GB/s, fraction of the HBM roofline).
+
+One step = one pass of the whole decode path over the workload: Huffman
+decoding of every sub-block, then LZ77 resolution of every block, for the
+workload's MRR stream and its DE stream, in one persistent launch of the
+batched decoder.  Inputs (compressed streams and block indexes) are resident
+in device memory before the timed region; the decompressed output (2 x 256 MiB
+for the default workload) is larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
+slow, obviously correct serial decoder) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+KiB, MiB, GiB = 1 << 10, 1 << 20, 1 << 30
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("gmp_decode.cu", "gmp_internal.h"):
+        with open(os.path.join(ROOT, "paper_1606_00519_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_unit():
+    """DRAM bytes per decompressed byte of the decode kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "decode_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if t.get("kernel_source_sha256_16") == _kernel_source_hash():
+            return float(t["dram_bytes_per_output_byte"]), t
+    except Exception:
+        pass
+    return None, None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", f"-lms", str(period_ms)],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s, p in zip(sm, pw)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+def _dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return rank, world, local, dist
+    return rank, world, local, None
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_workload(name: str, size: int | None = None):
+    """(workload, data, {mode: stream}) using the product compressor."""
+    import paper_1606_00519_gb300 as gmp
+    w = datagen.WORKLOADS[name]
+    data = w.data(size)
+    streams = {}
+    for mode in ("mrr", "de"):
+        streams[mode] = gmp.compress(data, w.block_size, w.n_sub, w.window, de=(mode == "de"))
+    return w, data, streams
+
+
+def cpu_oracle_sample(streams, budget_s: float, max_blocks: int | None = None):
+    """Time the oracle's serial decoder on a bounded sample of blocks (taken
+    round-robin from the streams, from the start).  Returns (bytes, seconds,
+    description)."""
+    import oracle
+    infos = {m: oracle.stream_info(s) for m, s in streams.items()}
+    done_bytes, t0, nblk = 0, time.perf_counter(), 0
+    b = 0
+    while True:
+        progressed = False
+        for m, s in streams.items():
+            if b < infos[m].n_blocks:
+                out = oracle.decompress_block(s, b)
+                done_bytes += out.size
+                nblk += 1
+                progressed = True
+        b += 1
+        el = time.perf_counter() - t0
+        if not progressed or el >= budget_s or (max_blocks and nblk >= max_blocks):
+            break
+    el = time.perf_counter() - t0
+    desc = f"first {b} blocks of each of the {len(streams)} streams ({nblk} blocks, {done_bytes} bytes), 1 thread"
+    return done_bytes, el, desc
+
+
+def run_reference(args):
+    rank, world, local, dist = _dist_init(args)
+    if rank != 0:
+        return
+    w, data, streams = make_workload(args.workload, args.size)
+    # each step decodes a bounded sample (the serial oracle is slow)
+    per_step_blocks = args.ref_blocks
+    for _ in range(args.warmup):
+        cpu_oracle_sample(streams, 1e9, max_blocks=min(4, per_step_blocks))
+    tot_b, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        nb, el, desc = cpu_oracle_sample(streams, 1e9, max_blocks=per_step_blocks)
+        tot_b += nb
+        tot_t += el
+    gbs = tot_b / tot_t / 1e9
+    line = {"impl": "reference", "metric": "decompressed GB/s", "value": gbs, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": _config(w, streams, data),
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: {desc}"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(w, streams, data):
+    return {"workload": f"{w.name}: {w.size // MiB} MiB {w.kind}, {w.block_size // KiB} KiB blocks, "
+                        f"K={w.n_sub} sub-blocks, {w.window // KiB} KiB window, MRR and DE streams",
+            "bytes_per_stream": int(data.size), "block_size": w.block_size, "n_sub": w.n_sub,
+            "window": w.window, "cwl": 12,
+            "ratio_mrr": round(data.size / streams["mrr"].size, 4),
+            "ratio_de": round(data.size / streams["de"].size, 4),
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+def run_gmp(args):
+    import torch
+    import paper_1606_00519_gb300 as gmp
+
+    rank, world, local, dist = _dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, data, streams = make_workload(args.workload, args.size)
+    modes = ["mrr", "de"]
+    ds = {m: gmp.DeviceStream(streams[m], device=dev) for m in modes}
+    outs = {m: torch.empty(data.size, dtype=torch.uint8, device=dev) for m in modes}
+    ctx = gmp.Context(device=local, max_block_out=w.block_size, warps_per_cta=args.warps_per_cta,
+                      collect_stats=False)
+    table = gmp.make_file_table([ds[m].file_desc(outs[m]) for m in modes], device=dev)
+    status = torch.zeros(len(modes), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out_bytes = data.size * len(modes)
+    comp_bytes = sum(ds[m].comp_bytes for m in modes)
+
+    def step():
+        ctx.decompress_batch(table, len(modes), status, stream)
+
+    # correctness of the timed configuration (byte-exact against the input)
+    step()
+    torch.cuda.synchronize()
+    ref = torch.from_numpy(data).to(dev)
+    st = status.cpu().numpy()
+    ok = bool(np.all(st == 0)) and all(bool(torch.equal(outs[m], ref)) for m in modes)
+    del ref
+    if not ok:
+        raise SystemExit(f"bench: decoded output is not byte-exact (status {st.tolist()})")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    _barrier(dist)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launch_ms = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        launch_ms.append((a, b))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    el_ms = ev0.elapsed_time(ev1)
+    per_launch = [a.elapsed_time(b) for a, b in launch_ms]
+    clk = clocks.stop() if clocks else None
+    el_ms = _max_over_ranks(dist, el_ms)
+    total_bytes = _sum_over_ranks(dist, float(out_bytes * args.steps))
+    value = total_bytes / (el_ms / 1e3) / 1e9
+
+    # per-mode throughput (each stream in its own launch), for context
+    per_mode = {}
+    for m in modes:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st1 = torch.zeros(1, dtype=torch.int32, device=dev)
+        ctx.decompress_into(ds[m], outs[m], st1, stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        reps = max(3, args.steps // 2)
+        for _ in range(reps):
+            ctx.decompress_into(ds[m], outs[m], st1, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        per_mode[m] = round(data.size * reps / (a.elapsed_time(b) / 1e3) / 1e9, 2)
+
+    # end to end through the public host-to-host call: pinned host input,
+    # H2D of the compressed stream, decode, D2H of the decompressed bytes
+    pin_in = {m: torch.from_numpy(streams[m].copy()).pin_memory() for m in modes}
+    pin_out = {m: torch.empty(data.size, dtype=torch.uint8).pin_memory() for m in modes}
+    e2e_ctx = ctx
+    for m in modes:  # allocate staging once, outside the timed region
+        e2e_ctx.decompress_host(pin_in[m].numpy(), pin_out[m].numpy(), stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    e2e_steps = max(2, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for m in modes:
+            _, stv = e2e_ctx.decompress_host(pin_in[m].numpy(), pin_out[m].numpy(), stream)
+            if stv != 0:
+                raise SystemExit("bench: e2e decode failed")
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_val = _sum_over_ranks(dist, float(out_bytes * e2e_steps)) / e2e_s / 1e9
+    if not all(np.array_equal(pin_out[m].numpy(), data) for m in modes):
+        raise SystemExit("bench: e2e output is not byte-exact")
+
+    if rank != 0:
+        return
+    hbm_peak, peak_kind = _peaks()
+    launch_avg_ms = float(np.mean(per_launch))
+    algo_bytes = comp_bytes + out_bytes  # compressed read + decompressed written
+    achieved = algo_bytes / (launch_avg_ms / 1e3) / 1e9
+    tpu, tinfo = _traffic_per_unit()
+    line = {
+        "metric": "decompressed GB/s", "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {**_config(w, streams, data), "parallelism": f"replicas x{world}",
+                   "warps_per_cta": args.warps_per_cta or 4, "per_mode_gbs": per_mode},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
+                     "traffic": (round(tpu * out_bytes) if tpu else None),
+                     "kernel": "gmp::decode_kernel (persistent; one launch per step)",
+                     "algorithmic_bytes_per_launch": int(algo_bytes),
+                     "decompressed_frac_of_roofline": round(
+                         value / (hbm_peak * (out_bytes / algo_bytes)), 4)},
+        "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": int(comp_bytes),
+                "d2h_bytes_per_step": int(out_bytes)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        nb, el, desc = cpu_oracle_sample(streams, args.cpu_budget)
+        line["cpu_baseline"] = {"value": round(nb / el / 1e9, 5), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gmp", choices=["gmp", "reference"])
+    ap.add_argument("--workload", default="text256m", choices=sorted(datagen.WORKLOADS))
+    ap.add_argument("--size", type=int, default=None, help="override bytes per stream")
+    ap.add_argument("--warps-per-cta", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
+    ap.add_argument("--ref-blocks", type=int, default=16, help="oracle blocks per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gmp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * gmp.h - C ABI of the GB300 Gompresso-style decompressor (libgmp.so).
+ *
+ * Method: "Massively-Parallel Lossless Data Decompression" (Sitaridi, Mueller,
+ * Kaldewey, Lohman, Ross; arXiv:1606.00519).  A stream is cut into blocks that
+ * are compressed independently (Sec. 3.1).  Decompression of a block
+ * Huffman-decodes its sub-blocks in parallel, one lane per sub-block, with
+ * lookup tables of both trees in on-chip memory (Sec. 3.2.1), then resolves
+ * the block's LZ77 sequences 32 at a time in one warp: two exclusive prefix
+ * sums by shuffle, literal copy, then back-reference copy (Sec. 3.2.2), either
+ * by Multi-Round Resolution (Fig. 5, Sec. 4.1) or, for streams written with
+ * Dependency Elimination, in a single pass (Fig. 6, Sec. 4.2).
+ *
+ * Conventions for every function:
+ *   - Return value: GMP_OK (0) or a negative gmp_error.  No exception crosses
+ *     the ABI.  Argument and launch errors are returned synchronously.
+ *   - Data errors found while decoding (a corrupt stream) are asynchronous:
+ *     the kernel writes a positive gmp_status into the caller's int32 status
+ *     word (first error wins) and abandons the damaged block; read it after
+ *     the stream has synchronised.  The output of a damaged block is
+ *     undefined; other blocks are still decoded.
+ *   - "device" pointers are CUDA device (or managed) memory of the context's
+ *     device; "host" pointers are ordinary host memory.  The caller owns every
+ *     buffer it passes; the library never frees caller memory.
+ *   - A context owns its scratch memory and is used by one stream at a time:
+ *     calls on one context must be ordered on one CUDA stream.  Use one
+ *     context per concurrent stream.
+ *
+ * Stream format (version 1; integers little-endian).  Written by
+ * gmp_compress, read by the decoders.  The paper gives the structure (a file
+ * header, then blocks, each with two canonical Huffman trees, sub-blocks with
+ * their size in bits, and the bitstream; Sec. 3.1); the field layout is this
+ * project's.
+ *   File header, 64 bytes:
+ *     0  "GMP1"            4  u16 version = 1      6  u16 flags (bit0 DE, bit1 Huffman = 1)
+ *     8  u32 block_size   12  u16 n_sub (K, 1..64) 14 u8 cwl (1..12)  15 u8 0
+ *    16  u32 window (1..32768)  20 u8 min_match = 3  21 u8 max_match (3..64)  22 u16 0
+ *    24  u64 orig_size    32  u64 n_blocks         40 u64 stream_bytes   48 16 bytes 0
+ *   Block offset table at 64: u64 per block, byte offset of the block from the
+ *   start of the stream (a multiple of 16).  The stream ends with >= 16 zero
+ *   bytes of padding.
+ *   Block, at a 16-byte aligned offset:
+ *     0  u32 n_seq   4 u32 out_bytes (block_size, except the last block)
+ *     8  160 bytes: 4-bit code lengths of the 319 literal/length symbols
+ *        (symbol s in byte s/2, low nibble for even s; 0 = unused)
+ *   168  15 bytes: 4-bit code lengths of the 30 offset symbols   183 9 bytes 0
+ *   192  n_sub entries {u32 bit_len, u32 out_bytes, u32 n_seq}: per sub-block
+ *        its size in bits (Sec. 3.1), and two extensions of this format, its
+ *        decompressed size and sequence count
+ *   then, at the next 16-byte boundary, the bitstream: the sub-blocks' bits
+ *   back to back (sub-block j starts at the sum of the earlier bit_len),
+ *   LSB-first within bytes, Huffman codes sent most significant bit first,
+ *   zero-padded to a 16-byte boundary.
+ *   Literal/length symbols: 0..255 literal byte; 256 end of a block whose last
+ *   sequence has no back-reference; 257..318 match length 3..64, followed by
+ *   an offset symbol.  Offset symbol for distance d, v = d - 1: v < 4 gives
+ *   symbol v; otherwise, with k = floor(log2 v), symbol 2k + bit (k-1) of v,
+ *   followed by k-1 extra bits holding v mod 2^(k-1), LSB-first.
+ *   Sub-blocks: a block's n_seq sequences are cut into K runs of
+ *   ceil(n_seq/K) sequences (trailing runs may be short or empty).  A
+ *   sequence is a literal string followed by one back-reference (Sec. 3.2.2).
+ *   Canonical codes (Sec. 3.1): codes of each length are consecutive in
+ *   symbol order; the first code of length L is (first(L-1) + count(L-1)) << 1.
+ *   DE flag: every back-reference of a 32-sequence group (numbered from the
+ *   block start) reads only bytes produced before the group's copies start:
+ *   bytes before the group, the group's literal strings, or earlier bytes of
+ *   its own copy.  The decoder checks this per group and falls back to MRR for
+ *   a group that breaks it, so a wrong flag costs speed, never correctness.
+ */
+#ifndef GMP_H_
+#define GMP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GMP_VERSION 1
+
+typedef enum {
+  GMP_OK = 0,
+  GMP_ERR_INVALID_ARG = -1, /* null pointer, bad size or alignment, bad option */
+  GMP_ERR_CAPACITY = -2,    /* a caller buffer or the context's scratch is too small */
+  GMP_ERR_CUDA = -3,        /* a CUDA runtime call failed (see gmp_last_cuda_error) */
+  GMP_ERR_UNSUPPORTED = -4, /* valid stream feature this build does not decode */
+  GMP_ERR_FORMAT = -5,      /* host-side parse found a malformed stream header */
+  GMP_ERR_NOMEM = -6        /* host allocation failed */
+} gmp_error;
+
+/* Values written to the caller's int32 status word by the decoder. */
+typedef enum {
+  GMP_STATUS_OK = 0,
+  GMP_STATUS_BAD_HEADER = 1,        /* block header inconsistent (sizes, code lengths, Kraft) */
+  GMP_STATUS_CORRUPT_SYMBOL = 2,    /* bit pattern with no code, or end symbol before the end */
+  GMP_STATUS_BITSTREAM = 3,         /* a sub-block read past its stored size or did not use it all */
+  GMP_STATUS_BAD_OFFSET = 4,        /* distance 0, beyond the window, or before the block start */
+  GMP_STATUS_OUTPUT_OVERRUN = 5,    /* decoded sizes disagree with the header or exceed out_cap */
+  GMP_STATUS_MRR_NO_PROGRESS = 6,   /* a resolution round made no progress (cannot happen on valid input) */
+  GMP_STATUS_CAPACITY = 7           /* a block needs more scratch than the context reserved */
+} gmp_status;
+
+/* ------------------------------------------------------------------------ */
+/* Stream header and block index (host, no CUDA).                           */
+
+typedef struct {
+  uint32_t version, flags, block_size, n_sub, cwl, window, min_match, max_match;
+  uint64_t orig_size, n_blocks, stream_bytes;
+  /* filled by gmp_index_build from the block headers: */
+  uint32_t max_block_out, max_block_seq;
+} gmp_stream_info;
+
+/* One block of a stream: where its compressed bytes are (relative to the
+   stream start) and where its output goes (relative to the output start). */
+typedef struct {
+  uint64_t comp_offset, comp_bytes, out_offset, out_bytes;
+} gmp_block_ref;
+
+/* Parse the 64-byte file header.  host_stream: host pointer to at least
+   `bytes` bytes of the stream.  Returns GMP_ERR_FORMAT on a bad header. */
+int gmp_stream_info_parse(const void* host_stream, size_t bytes, gmp_stream_info* info);
+
+/* Build the block index (Sec. 3.2.2: each warp finds its block from the block
+   offsets; all blocks but the last have block_size bytes of output).
+   host_stream: the whole stream in host memory.  out: host array of `cap`
+   entries (may be NULL with cap 0 to query *n_blocks).  Also checks every
+   block header's sizes against the file header and fills info (may be NULL).
+   Returns GMP_ERR_CAPACITY if cap < n_blocks (with *n_blocks set). */
+int gmp_index_build(const void* host_stream, size_t bytes, gmp_block_ref* out, size_t cap, size_t* n_blocks,
+                    gmp_stream_info* info);
+
+/* ------------------------------------------------------------------------ */
+/* Compressor (host, multi-threaded over blocks).  Not on the decode path; it
+   writes the format above (Sec. 3.1: block split, LZ77, two length-limited
+   canonical Huffman trees per block, sub-blocks; Sec. 4.2 for DE).         */
+
+typedef struct {
+  uint32_t block_size;  /* bytes per block (default 256 KiB) */
+  uint32_t n_sub;       /* K sub-blocks per block, 1..64 (default 32) */
+  uint32_t window;      /* LZ77 window, 1..32768 (default 32 KiB) */
+  uint32_t cwl;         /* Huffman code length limit, 1..12 (default 12) */
+  uint32_t max_match;   /* 3..64 (default 64) */
+  uint32_t chain_depth; /* match candidates tried per position (default 64) */
+  uint32_t de;          /* 1: Dependency Elimination (Sec. 4.2), 0: plain (MRR) */
+  uint32_t n_threads;   /* host threads, 0 = all cores */
+} gmp_compress_opts;
+
+void gmp_compress_opts_default(gmp_compress_opts* o);
+/* Upper bound of the compressed size of n input bytes. */
+size_t gmp_compress_bound(size_t n, const gmp_compress_opts* o);
+/* host_in: n bytes; host_out: cap bytes.  *out_bytes receives the stream size.
+   GMP_ERR_CAPACITY if cap < the stream size (use gmp_compress_bound). */
+int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* o, void* host_out, size_t cap,
+                 size_t* out_bytes);
+
+/* ------------------------------------------------------------------------ */
+/* Decoder context. */
+
+typedef struct gmp_context gmp_context;
+
+typedef struct {
+  uint32_t max_block_out;   /* largest block output the scratch must hold (default 256 KiB) */
+  uint32_t warps_per_cta;   /* 0 = tuned default */
+  uint32_t ctas_per_sm;     /* 0 = as many as fit */
+  uint32_t collect_stats;   /* 1: count groups and MRR rounds (small cost) */
+  uint32_t max_files;       /* largest n_files of gmp_decompress_batch (default 65536) */
+} gmp_context_opts;
+
+void gmp_context_opts_default(gmp_context_opts* o);
+/* Creates a context on `device`: allocates the scratch of one persistent
+   launch (one slot per resident warp) and a small device work counter.
+   opts may be NULL. */
+int gmp_context_create(gmp_context** ctx, int device, const gmp_context_opts* opts);
+void gmp_context_destroy(gmp_context* ctx);
+/* Change launch shape (an autotuner result); reallocates scratch if needed. */
+int gmp_context_set_launch(gmp_context* ctx, uint32_t warps_per_cta, uint32_t ctas_per_sm);
+/* Bytes of device scratch the context holds. */
+size_t gmp_context_scratch_bytes(const gmp_context* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Decompression of one stream (Sec. 3.2): one persistent launch, a warp per
+   block taken from a work counter.
+   d_comp: device, the whole stream (16-byte aligned); comp_bytes its size.
+   d_index: device array of n_blocks gmp_block_ref (from gmp_index_build).
+   d_out: device output buffer of out_cap bytes (16-byte aligned for the
+   vectorised store path; other alignments use byte stores).
+   d_status: device int32, set to 0 by this call (stream-ordered) and then to
+   the first gmp_status error if any.  stream: a cudaStream_t (NULL = legacy
+   default stream).  Asynchronous; no allocation. */
+int gmp_decompress(gmp_context* ctx, const uint8_t* d_comp, size_t comp_bytes, const gmp_block_ref* d_index,
+                   size_t n_blocks, uint8_t* d_out, size_t out_cap, int32_t* d_status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched decompression: many independent streams in ONE persistent launch.
+   Every (file, block) pair is a work item; warps take items from a device
+   counter, so files of uneven sizes share the GPU.                         */
+typedef struct {
+  const uint8_t* comp;          /* device, 16-byte aligned stream */
+  uint64_t comp_bytes;
+  const gmp_block_ref* index;   /* device, n_blocks entries */
+  uint64_t n_blocks;
+  uint8_t* out;                 /* device output buffer */
+  uint64_t out_cap;
+} gmp_file_desc;
+
+/* d_files: device array of n_files descriptors.  d_status: device array of
+   n_files int32, each zeroed by this call and then set to the file's first
+   error.  A small single-CTA kernel first forms the work-item prefix over the
+   files' block counts in context scratch (n_files <= max_files of the
+   context, else GMP_ERR_CAPACITY); the persistent kernel then maps each item
+   to its (file, block) by binary search.  Asynchronous; no allocation;
+   capturable in a CUDA graph (gmp_batch_graph_create does that). */
+int gmp_decompress_batch(gmp_context* ctx, const gmp_file_desc* d_files, size_t n_files, int32_t* d_status,
+                         void* stream);
+
+/* A CUDA graph holding one batched launch (counter reset + status reset +
+   the persistent kernel), replayed with gmp_graph_launch. */
+typedef struct gmp_graph gmp_graph;
+int gmp_batch_graph_create(gmp_context* ctx, const gmp_file_desc* d_files, size_t n_files, int32_t* d_status,
+                           void* stream, gmp_graph** g);
+int gmp_graph_launch(gmp_graph* g, void* stream);
+void gmp_graph_destroy(gmp_graph* g);
+
+/* ------------------------------------------------------------------------ */
+/* Statistics of the last launches since gmp_stats_reset (collect_stats=1):
+   32-sequence groups resolved, MRR rounds, groups of a DE stream that broke
+   the DE property and were resolved by MRR, blocks decoded. */
+typedef struct {
+  uint64_t groups, rounds, de_fallback_groups, blocks, max_rounds;
+} gmp_stats;
+int gmp_stats_reset(gmp_context* ctx, void* stream);
+int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device */
+
+/* ------------------------------------------------------------------------ */
+/* Host-to-host convenience (the paper's "(In/Out)" mode, Sec. 5.4): copies a
+   host stream to the device, decodes it and copies the output back.  Uses
+   (and grows) device staging buffers owned by the context.  host_out: out_cap
+   bytes.  *status receives the decoder status.  Synchronous. */
+int gmp_decompress_host(gmp_context* ctx, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,
+                        int32_t* status, void* stream);
+
+/* Last CUDA error string of this thread (for GMP_ERR_CUDA). */
+const char* gmp_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMP_H_ */

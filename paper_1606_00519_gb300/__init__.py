@@ -1,0 +1,251 @@
+"""GB300-native Gompresso-style decompression (arXiv:1606.00519).
+
+Thin Python binding over libgmp.so (C ABI in include/gmp.h): argument
+marshalling only.  Every decoding step runs in the library's CUDA kernels;
+PyTorch provides device memory and streams.  There is no CPU fallback: if the
+library is not built or no GPU is present, the decode calls raise.
+
+Typical use::
+
+    import paper_1606_00519_gb300 as gmp
+    stream = gmp.compress(data, block_size=256 << 10, n_sub=32, window=32768, de=True)
+    dev = gmp.DeviceStream(stream)               # stream + block index on the GPU
+    ctx = gmp.Context()
+    out, status = ctx.decompress(dev)            # torch.uint8 CUDA tensor
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native
+from ._native import BlockRef, CompressOpts, ContextOpts, FileDesc, Stats, StreamInfo
+
+OK = 0
+STATUS_NAMES = {0: "OK", 1: "BAD_HEADER", 2: "CORRUPT_SYMBOL", 3: "BITSTREAM", 4: "BAD_OFFSET",
+                5: "OUTPUT_OVERRUN", 6: "MRR_NO_PROGRESS", 7: "CAPACITY"}
+ERROR_NAMES = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "CUDA", -4: "UNSUPPORTED", -5: "FORMAT", -6: "NOMEM"}
+
+
+class GmpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {ERROR_NAMES.get(code, code)}"
+        if code == -3:
+            msg += f" ({_native.lib().gmp_last_cuda_error().decode()})"
+        super().__init__(msg)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise GmpError(rc, what)
+
+
+def _np_bytes(x) -> np.ndarray:
+    if isinstance(x, np.ndarray):
+        return np.ascontiguousarray(x.reshape(-1).view(np.uint8))
+    return np.frombuffer(bytes(x), dtype=np.uint8)
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+# --------------------------------------------------------------------------
+# host side: compressor, header, block index
+
+def compress(data, block_size: int = 256 << 10, n_sub: int = 32, window: int = 32768, cwl: int = 12,
+             max_match: int = 64, chain_depth: int = 64, de: bool = False, n_threads: int = 0) -> np.ndarray:
+    """Compress host bytes into the stream format of include/gmp.h (host,
+    multi-threaded over blocks)."""
+    L = _native.lib()
+    src = _np_bytes(data)
+    o = CompressOpts(block_size, n_sub, window, cwl, max_match, chain_depth, 1 if de else 0, n_threads)
+    cap = L.gmp_compress_bound(src.size, ctypes.byref(o))
+    out = np.empty(cap, np.uint8)
+    n = ctypes.c_size_t()
+    _check(L.gmp_compress(_ptr(src) if src.size else None, src.size, ctypes.byref(o), _ptr(out), cap,
+                          ctypes.byref(n)), "gmp_compress")
+    return out[:n.value]
+
+
+def stream_info(stream) -> StreamInfo:
+    s = _np_bytes(stream)
+    info = StreamInfo()
+    _check(_native.lib().gmp_stream_info_parse(_ptr(s), s.size, ctypes.byref(info)), "gmp_stream_info_parse")
+    return info
+
+
+def index_build(stream):
+    """(index as an (n_blocks, 4) uint64 array, StreamInfo)."""
+    L = _native.lib()
+    s = _np_bytes(stream)
+    n = ctypes.c_size_t()
+    info = StreamInfo()
+    _check(L.gmp_index_build(_ptr(s), s.size, None, 0, ctypes.byref(n), ctypes.byref(info)), "gmp_index_build")
+    idx = np.zeros((max(n.value, 1), 4), np.uint64)
+    _check(L.gmp_index_build(_ptr(s), s.size, idx.ctypes.data_as(ctypes.POINTER(BlockRef)), n.value,
+                             ctypes.byref(n), ctypes.byref(info)), "gmp_index_build")
+    return idx[:n.value], info
+
+
+@dataclass
+class DeviceStream:
+    """A compressed stream and its block index resident on the GPU."""
+    comp: object          # torch.uint8 CUDA tensor (16-byte aligned)
+    index: object         # torch.uint64-as-int64 CUDA tensor, (n_blocks, 4)
+    info: StreamInfo
+    n_blocks: int
+    comp_bytes: int
+
+    def __init__(self, stream, device=None):
+        torch = _torch()
+        s = _np_bytes(stream)
+        idx, info = index_build(s)
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.comp = torch.from_numpy(s.copy()).to(dev)
+        self.index = torch.from_numpy(idx.view(np.int64).copy()).to(dev)
+        self.info = info
+        self.n_blocks = int(idx.shape[0])
+        self.comp_bytes = int(s.size)
+
+    @property
+    def orig_size(self) -> int:
+        return int(self.info.orig_size)
+
+    def file_desc(self, out, out_cap: int | None = None) -> FileDesc:
+        return FileDesc(self.comp.data_ptr(), self.comp_bytes, self.index.data_ptr(), self.n_blocks,
+                        out.data_ptr(), out.numel() if out_cap is None else out_cap)
+
+
+class Context:
+    """A decoder context (scratch for one persistent launch) on one device."""
+
+    def __init__(self, device: int | None = None, max_block_out: int = 256 << 10, warps_per_cta: int = 0,
+                 ctas_per_sm: int = 0, collect_stats: bool = False, max_files: int = 65536):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the decoder runs only on the GPU")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._L = _native.lib()
+        o = ContextOpts(max_block_out, warps_per_cta, ctas_per_sm, 1 if collect_stats else 0, max_files)
+        h = ctypes.c_void_p()
+        _check(self._L.gmp_context_create(ctypes.byref(h), self.device, ctypes.byref(o)), "gmp_context_create")
+        self._h = h
+        self.max_block_out = max_block_out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.gmp_context_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def set_launch(self, warps_per_cta: int, ctas_per_sm: int = 0):
+        _check(self._L.gmp_context_set_launch(self._h, warps_per_cta, ctas_per_sm), "gmp_context_set_launch")
+
+    def scratch_bytes(self) -> int:
+        return int(self._L.gmp_context_scratch_bytes(self._h))
+
+    def decompress_into(self, ds: DeviceStream, out, status, stream=None):
+        """Asynchronous decode of `ds` into the uint8 CUDA tensor `out`;
+        `status` is an int32 CUDA tensor of >= 1 element."""
+        _check(self._L.gmp_decompress(self._h, ctypes.c_void_p(ds.comp.data_ptr()), ds.comp_bytes,
+                                      ctypes.c_void_p(ds.index.data_ptr()), ds.n_blocks,
+                                      ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                      ctypes.c_void_p(status.data_ptr()), _stream_handle(stream)),
+               "gmp_decompress")
+
+    def decompress(self, ds: DeviceStream, stream=None):
+        """Decode into a new CUDA tensor; returns (out, status) where status is
+        read after synchronising the stream."""
+        torch = _torch()
+        out = torch.empty(max(ds.orig_size, 16), dtype=torch.uint8, device=ds.comp.device)
+        st = torch.zeros(1, dtype=torch.int32, device=ds.comp.device)
+        self.decompress_into(ds, out, st, stream)
+        status = int(st.item())
+        return out[:ds.orig_size], status
+
+    def decompress_batch(self, files_dev, n_files: int, status, stream=None):
+        """files_dev: CUDA tensor holding n_files FileDesc records (see
+        make_file_table); status: int32 CUDA tensor of n_files."""
+        _check(self._L.gmp_decompress_batch(self._h, ctypes.c_void_p(files_dev.data_ptr()), n_files,
+                                            ctypes.c_void_p(status.data_ptr()), _stream_handle(stream)),
+               "gmp_decompress_batch")
+
+    def batch_graph(self, files_dev, n_files: int, status) -> "Graph":
+        g = ctypes.c_void_p()
+        _check(self._L.gmp_batch_graph_create(self._h, ctypes.c_void_p(files_dev.data_ptr()), n_files,
+                                              ctypes.c_void_p(status.data_ptr()), None, ctypes.byref(g)),
+               "gmp_batch_graph_create")
+        return Graph(self._L, g)
+
+    def stats_reset(self, stream=None):
+        _check(self._L.gmp_stats_reset(self._h, _stream_handle(stream)), "gmp_stats_reset")
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._L.gmp_stats_read(self._h, ctypes.byref(s)), "gmp_stats_read")
+        return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+
+    def decompress_host(self, stream, out: np.ndarray | None = None, cuda_stream=None):
+        """Host stream in, host bytes out (H2D + decode + D2H, synchronous)."""
+        s = _np_bytes(stream)
+        info = stream_info(s)
+        if out is None:
+            out = np.empty(max(info.orig_size, 1), np.uint8)
+        st = ctypes.c_int32()
+        _check(self._L.gmp_decompress_host(self._h, _ptr(s), s.size, _ptr(out), out.size, ctypes.byref(st),
+                                           _stream_handle(cuda_stream)), "gmp_decompress_host")
+        return out[:info.orig_size], st.value
+
+
+class Graph:
+    def __init__(self, L, h):
+        self._L = L
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(self._L.gmp_graph_launch(self._h, _stream_handle(stream)), "gmp_graph_launch")
+
+    def close(self):
+        if self._h and self._h.value:
+            self._L.gmp_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_file_table(descs, device=None):
+    """Pack FileDesc records into a CUDA tensor for the batched calls."""
+    torch = _torch()
+    arr = (FileDesc * len(descs))(*descs)
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    return torch.from_numpy(raw).to(dev)

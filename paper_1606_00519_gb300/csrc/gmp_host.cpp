@@ -1,0 +1,384 @@
+// gmp_host.cpp - host runtime of libgmp: stream header and block index,
+// decoder contexts (scratch sizing, launch shape), launches, CUDA graphs of
+// batched launches, statistics, and the host-to-host convenience call.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gmp.h"
+#include "gmp_internal.h"
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_cuda_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return GMP_ERR_CUDA;
+}
+#define GMP_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+uint32_t rd16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+uint32_t rd32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+uint64_t rd64(const uint8_t* p) { return (uint64_t)rd32(p) | ((uint64_t)rd32(p + 4) << 32); }
+
+// Restores the caller's current device when a call returns.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct gmp_context {
+  int device = 0;
+  int sm_count = 0;
+  gmp_context_opts opts{};
+  gmp::LaunchShape shape{};
+  uint32_t max_seq = 0, max_out = 0;
+  uint64_t slot_bytes = 0;
+  uint8_t* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  unsigned long long* counter = nullptr;  // work counter
+  unsigned long long* stats = nullptr;    // 5 counters
+  uint64_t* item_start = nullptr;         // batch prefix, max_files + 1
+  // staging of gmp_decompress_host
+  uint8_t* h_comp = nullptr;
+  size_t h_comp_cap = 0;
+  uint8_t* h_out = nullptr;
+  size_t h_out_cap = 0;
+  gmp_block_ref* h_index = nullptr;
+  size_t h_index_cap = 0;
+  int32_t* h_status = nullptr;
+};
+
+struct gmp_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+const char* gmp_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int gmp_stream_info_parse(const void* host_stream, size_t bytes, gmp_stream_info* info) {
+  if (!host_stream || !info) return GMP_ERR_INVALID_ARG;
+  const uint8_t* s = static_cast<const uint8_t*>(host_stream);
+  if (bytes < gmp::kHeaderBytes || memcmp(s, "GMP1", 4) != 0) return GMP_ERR_FORMAT;
+  gmp_stream_info I{};
+  I.version = rd16(s + 4);
+  I.flags = rd16(s + 6);
+  I.block_size = rd32(s + 8);
+  I.n_sub = rd16(s + 12);
+  I.cwl = s[14];
+  I.window = rd32(s + 16);
+  I.min_match = s[20];
+  I.max_match = s[21];
+  I.orig_size = rd64(s + 24);
+  I.n_blocks = rd64(s + 32);
+  I.stream_bytes = rd64(s + 40);
+  if (I.version != GMP_VERSION) return GMP_ERR_UNSUPPORTED;
+  if (!(I.flags & 2u)) return GMP_ERR_UNSUPPORTED;  // byte-level streams are not decoded by this build
+  if (I.block_size == 0 || I.n_sub == 0 || I.n_sub > gmp::kMaxSub || I.cwl == 0 || I.cwl > 12 || I.window == 0 ||
+      I.window > 32768 || I.min_match != 3 || I.max_match < 3 || I.max_match > 64)
+    return GMP_ERR_FORMAT;
+  if (I.n_blocks != (I.orig_size + I.block_size - 1) / I.block_size) return GMP_ERR_FORMAT;
+  if (I.stream_bytes > bytes || I.stream_bytes < gmp::kHeaderBytes + 8 * I.n_blocks) return GMP_ERR_FORMAT;
+  *info = I;
+  return GMP_OK;
+}
+
+int gmp_index_build(const void* host_stream, size_t bytes, gmp_block_ref* out, size_t cap, size_t* n_blocks,
+                    gmp_stream_info* info) {
+  if (!host_stream || !n_blocks) return GMP_ERR_INVALID_ARG;
+  gmp_stream_info I;
+  int rc = gmp_stream_info_parse(host_stream, bytes, &I);
+  if (rc) return rc;
+  *n_blocks = (size_t)I.n_blocks;
+  if (cap < I.n_blocks) {
+    if (info) *info = I;
+    return out || cap ? GMP_ERR_CAPACITY : GMP_OK;
+  }
+  const uint8_t* s = static_cast<const uint8_t*>(host_stream);
+  const uint64_t table_end = gmp::kHeaderBytes + 8 * I.n_blocks;
+  const uint64_t blk_hdr = (gmp::kBlockFixed + 12ull * I.n_sub + 15) & ~15ull;
+  uint32_t max_out = 0, max_seq = 0;
+  for (uint64_t b = 0; b < I.n_blocks; b++) {
+    uint64_t off = rd64(s + gmp::kHeaderBytes + 8 * b);
+    uint64_t next = b + 1 < I.n_blocks ? rd64(s + gmp::kHeaderBytes + 8 * (b + 1)) : I.stream_bytes - 16;
+    if ((off & 15) || off < table_end || next < off + blk_hdr || next > I.stream_bytes) return GMP_ERR_FORMAT;
+    uint32_t n_seq = rd32(s + off), ob = rd32(s + off + 4);
+    uint64_t expect = b + 1 < I.n_blocks ? I.block_size : I.orig_size - b * (uint64_t)I.block_size;
+    if (ob != expect) return GMP_ERR_FORMAT;
+    out[b].comp_offset = off;
+    out[b].comp_bytes = next - off;
+    out[b].out_offset = b * (uint64_t)I.block_size;
+    out[b].out_bytes = ob;
+    max_out = std::max(max_out, ob);
+    max_seq = std::max(max_seq, n_seq);
+  }
+  I.max_block_out = max_out;
+  I.max_block_seq = max_seq;
+  if (info) *info = I;
+  return GMP_OK;
+}
+
+void gmp_context_opts_default(gmp_context_opts* o) {
+  o->max_block_out = 256u << 10;
+  o->warps_per_cta = 0;
+  o->ctas_per_sm = 0;
+  o->collect_stats = 0;
+  o->max_files = 65536;
+}
+
+static int context_alloc_scratch(gmp_context* c) {
+  // launch shape: persistent grid, as many CTAs per SM as fit
+  int wpc = c->opts.warps_per_cta ? (int)c->opts.warps_per_cta : 4;
+  if (wpc < 1 || wpc > 16) return GMP_ERR_INVALID_ARG;
+  size_t smem = (size_t)wpc * gmp::warp_smem_bytes();
+  GMP_CUDA(gmp::configure_kernel(smem));
+  int occ = 0;
+  GMP_CUDA(gmp::occupancy(wpc, smem, &occ));
+  if (occ < 1) return GMP_ERR_INVALID_ARG;
+  int per_sm = c->opts.ctas_per_sm ? std::min<int>((int)c->opts.ctas_per_sm, occ) : occ;
+  c->shape.grid = per_sm * c->sm_count;
+  c->shape.warps_per_cta = wpc;
+  c->shape.smem_bytes = smem;
+  // one scratch slot per resident warp: records (8 B per sequence; a block
+  // holds at most out/3 + 1 sequences) and the literal shadow (output layout
+  // plus 16 bytes of separation per sub-block)
+  c->max_out = c->opts.max_block_out;
+  c->max_seq = c->max_out / 3 + 2;
+  uint64_t rec = (uint64_t)c->max_seq * 8;
+  uint64_t shadow = (uint64_t)c->max_out + 16ull * gmp::kMaxSub + 64;
+  c->slot_bytes = (rec + shadow + 255) & ~255ull;
+  size_t need = (size_t)c->slot_bytes * (size_t)c->shape.grid * (size_t)wpc;
+  if (c->scratch && c->scratch_bytes >= need) return GMP_OK;
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  GMP_CUDA(cudaMalloc(&c->scratch, need));
+  c->scratch_bytes = need;
+  return GMP_OK;
+}
+
+int gmp_context_create(gmp_context** ctx, int device, const gmp_context_opts* opts) {
+  if (!ctx) return GMP_ERR_INVALID_ARG;
+  *ctx = nullptr;
+  gmp_context* c = new (std::nothrow) gmp_context();
+  if (!c) return GMP_ERR_NOMEM;
+  if (opts) c->opts = *opts;
+  else gmp_context_opts_default(&c->opts);
+  if (c->opts.max_block_out == 0 || c->opts.max_block_out > (64u << 20) || c->opts.max_files == 0) {
+    delete c;
+    return GMP_ERR_INVALID_ARG;
+  }
+  c->device = device;
+  DeviceGuard guard(device);
+  cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  int rc = context_alloc_scratch(c);
+  if (rc == GMP_OK) {
+    e = cudaMalloc(&c->counter, 64 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->item_start, (c->opts.max_files + 1) * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMemset(c->counter, 0, 64 * sizeof(unsigned long long));
+    if (e != cudaSuccess) rc = cuda_fail(e, "context alloc");
+    c->stats = c->counter + 8;
+  }
+  if (rc != GMP_OK) {
+    gmp_context_destroy(c);
+    return rc;
+  }
+  *ctx = c;
+  return GMP_OK;
+}
+
+void gmp_context_destroy(gmp_context* c) {
+  if (!c) return;
+  DeviceGuard guard(c->device);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->counter) cudaFree(c->counter);
+  if (c->item_start) cudaFree(c->item_start);
+  if (c->h_comp) cudaFree(c->h_comp);
+  if (c->h_out) cudaFree(c->h_out);
+  if (c->h_index) cudaFree(c->h_index);
+  if (c->h_status) cudaFree(c->h_status);
+  delete c;
+}
+
+int gmp_context_set_launch(gmp_context* c, uint32_t warps_per_cta, uint32_t ctas_per_sm) {
+  if (!c || warps_per_cta > 16) return GMP_ERR_INVALID_ARG;
+  DeviceGuard guard(c->device);
+  c->opts.warps_per_cta = warps_per_cta;
+  c->opts.ctas_per_sm = ctas_per_sm;
+  return context_alloc_scratch(c);
+}
+
+size_t gmp_context_scratch_bytes(const gmp_context* c) { return c ? c->scratch_bytes : 0; }
+
+int gmp_decompress(gmp_context* c, const uint8_t* d_comp, size_t comp_bytes, const gmp_block_ref* d_index,
+                   size_t n_blocks, uint8_t* d_out, size_t out_cap, int32_t* d_status, void* stream) {
+  if (!c || !d_status || (n_blocks && (!d_comp || !d_index || !d_out))) return GMP_ERR_INVALID_ARG;
+  if ((uintptr_t)d_comp & 15) return GMP_ERR_INVALID_ARG;
+  if (n_blocks && comp_bytes < gmp::kHeaderBytes) return GMP_ERR_INVALID_ARG;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  GMP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
+  if (n_blocks == 0) return GMP_OK;
+  GMP_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
+  gmp_file_desc F{d_comp, comp_bytes, d_index, n_blocks, d_out, out_cap};
+  gmp::LaunchShape shape = c->shape;
+  // no more CTAs than work items need
+  uint64_t warps_needed = n_blocks;
+  uint64_t ctas_needed = (warps_needed + shape.warps_per_cta - 1) / shape.warps_per_cta;
+  if ((uint64_t)shape.grid > ctas_needed) shape.grid = (int)ctas_needed;
+  GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, c->counter, c->scratch, c->slot_bytes,
+                              c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats, s));
+  return GMP_OK;
+}
+
+int gmp_decompress_batch(gmp_context* c, const gmp_file_desc* d_files, size_t n_files, int32_t* d_status,
+                         void* stream) {
+  if (!c || (n_files && (!d_files || !d_status))) return GMP_ERR_INVALID_ARG;
+  if (n_files > c->opts.max_files) return GMP_ERR_CAPACITY;
+  if (n_files == 0) return GMP_OK;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  GMP_CUDA(cudaMemsetAsync(d_status, 0, n_files * sizeof(int32_t), s));
+  GMP_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
+  GMP_CUDA(gmp::launch_batch_prefix(d_files, (uint32_t)n_files, c->item_start, s));
+  GMP_CUDA(gmp::launch_decode(c->shape, d_files, c->item_start, (uint32_t)n_files, nullptr, d_status, c->counter,
+                              c->scratch, c->slot_bytes, c->max_seq, c->max_out, c->stats,
+                              (int)c->opts.collect_stats, s));
+  return GMP_OK;
+}
+
+int gmp_batch_graph_create(gmp_context* c, const gmp_file_desc* d_files, size_t n_files, int32_t* d_status,
+                           void* stream, gmp_graph** g) {
+  if (!c || !g) return GMP_ERR_INVALID_ARG;
+  *g = nullptr;
+  DeviceGuard guard(c->device);
+  cudaStream_t cap;
+  GMP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  gmp_graph* gr = new (std::nothrow) gmp_graph();
+  if (!gr) {
+    cudaStreamDestroy(cap);
+    return GMP_ERR_NOMEM;
+  }
+  int rc = GMP_OK;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = gmp_decompress_batch(c, d_files, n_files, d_status, cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &gr->graph);
+    if (rc == GMP_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+  } else {
+    rc = cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  if (rc == GMP_OK) {
+    e = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+  }
+  cudaStreamDestroy(cap);
+  (void)stream;
+  if (rc != GMP_OK) {
+    gmp_graph_destroy(gr);
+    return rc;
+  }
+  *g = gr;
+  return GMP_OK;
+}
+
+int gmp_graph_launch(gmp_graph* g, void* stream) {
+  if (!g || !g->exec) return GMP_ERR_INVALID_ARG;
+  GMP_CUDA(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+  return GMP_OK;
+}
+
+void gmp_graph_destroy(gmp_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+int gmp_stats_reset(gmp_context* c, void* stream) {
+  if (!c) return GMP_ERR_INVALID_ARG;
+  DeviceGuard guard(c->device);
+  GMP_CUDA(cudaMemsetAsync(c->stats, 0, 5 * sizeof(unsigned long long), static_cast<cudaStream_t>(stream)));
+  return GMP_OK;
+}
+
+int gmp_stats_read(gmp_context* c, gmp_stats* out) {
+  if (!c || !out) return GMP_ERR_INVALID_ARG;
+  DeviceGuard guard(c->device);
+  unsigned long long v[5];
+  GMP_CUDA(cudaDeviceSynchronize());
+  GMP_CUDA(cudaMemcpy(v, c->stats, sizeof(v), cudaMemcpyDeviceToHost));
+  out->groups = v[0];
+  out->rounds = v[1];
+  out->de_fallback_groups = v[2];
+  out->blocks = v[3];
+  out->max_rounds = v[4];
+  return GMP_OK;
+}
+
+int gmp_decompress_host(gmp_context* c, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,
+                        int32_t* status, void* stream) {
+  if (!c || !host_stream || !status || (!host_out && out_cap)) return GMP_ERR_INVALID_ARG;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  size_t nb = 0;
+  gmp_stream_info info;
+  int rc = gmp_index_build(host_stream, bytes, nullptr, 0, &nb, &info);
+  if (rc) return rc;
+  if (info.orig_size > out_cap) return GMP_ERR_CAPACITY;
+  std::vector<gmp_block_ref> idx(nb);
+  rc = gmp_index_build(host_stream, bytes, idx.data(), nb, &nb, &info);
+  if (rc) return rc;
+  if (info.max_block_out > c->max_out) return GMP_ERR_CAPACITY;
+  auto grow = [&](auto** p, size_t* cap, size_t need) -> int {
+    if (*cap >= need) return GMP_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    GMP_CUDA(cudaMalloc((void**)p, need));
+    *cap = need;
+    return GMP_OK;
+  };
+  if ((rc = grow(&c->h_comp, &c->h_comp_cap, bytes))) return rc;
+  if ((rc = grow(&c->h_out, &c->h_out_cap, std::max<size_t>(info.orig_size, 16)))) return rc;
+  if ((rc = grow(&c->h_index, &c->h_index_cap, std::max<size_t>(nb, 1) * sizeof(gmp_block_ref)))) return rc;
+  if (!c->h_status) GMP_CUDA(cudaMalloc(&c->h_status, 16));
+  GMP_CUDA(cudaMemcpyAsync(c->h_comp, host_stream, bytes, cudaMemcpyHostToDevice, s));
+  if (nb) GMP_CUDA(cudaMemcpyAsync(c->h_index, idx.data(), nb * sizeof(gmp_block_ref), cudaMemcpyHostToDevice, s));
+  rc = gmp_decompress(c, c->h_comp, bytes, c->h_index, nb, c->h_out, info.orig_size, c->h_status, s);
+  if (rc) return rc;
+  if (info.orig_size) GMP_CUDA(cudaMemcpyAsync(host_out, c->h_out, info.orig_size, cudaMemcpyDeviceToHost, s));
+  GMP_CUDA(cudaMemcpyAsync(status, c->h_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GMP_CUDA(cudaStreamSynchronize(s));
+  return GMP_OK;
+}
+
+}  // extern "C"

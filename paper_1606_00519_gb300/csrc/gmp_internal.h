@@ -1,0 +1,39 @@
+// gmp_internal.h - declarations shared by the host runtime and the kernels of
+// libgmp.  Not part of the C ABI.
+#ifndef GMP_INTERNAL_H_
+#define GMP_INTERNAL_H_
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "gmp.h"
+
+namespace gmp {
+
+struct LaunchShape {
+  int grid;           // CTAs of the persistent launch
+  int warps_per_cta;  // one block of a stream per warp at a time
+  size_t smem_bytes;  // dynamic shared memory per CTA
+};
+
+size_t warp_smem_bytes();
+cudaError_t configure_kernel(size_t smem_bytes);
+cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm);
+cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, const uint64_t* item_start,
+                          uint32_t n_files, const gmp_file_desc* single, int32_t* status,
+                          unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint32_t max_seq,
+                          uint32_t max_out, unsigned long long* stats, int collect_stats, cudaStream_t stream);
+cudaError_t launch_batch_prefix(const gmp_file_desc* files, uint32_t n_files, uint64_t* item_start,
+                                cudaStream_t stream);
+
+// Stream-format constants (format version 1).
+constexpr uint32_t kHeaderBytes = 64;
+constexpr uint32_t kBlockFixed = 192;
+constexpr uint32_t kMaxSub = 64;
+constexpr uint32_t kLitLenSyms = 319;
+constexpr uint32_t kOffsetSyms = 30;
+
+}  // namespace gmp
+
+#endif  // GMP_INTERNAL_H_

@@ -1,0 +1,99 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every
+function include/gmp.h declares, parses stream headers and block indexes, and
+its compressor writes streams that the oracle validates and decodes back to
+the input."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "gmp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(gmp_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1606_00519_gb300 import _native
+    _native.build()
+    return _native.lib()
+
+
+def test_library_exports_every_declared_function(lib):
+    names = _declared_functions()
+    assert len(names) >= 19
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm103a_only():
+    from paper_1606_00519_gb300 import _native
+    assert _native.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_compressor_streams_validate_and_roundtrip(lib):
+    import paper_1606_00519_gb300 as gmp
+    for name, w in datagen.WORKLOADS.items():
+        data = w.data(3 * w.block_size + 777)
+        for mode in w.modes:
+            s = gmp.compress(data, w.block_size, w.n_sub, w.window, de=(mode == "de"))
+            assert np.array_equal(oracle.decompress(s), data)
+            r = oracle.validate(s)
+            assert r["rc"] == 0 and r["kraft_ok"] and r["offsets_ok"] and r["subblocks_ok"] and r["blocks_ok"]
+            if mode == "de":
+                assert r["de_weak_ok"]
+
+
+def test_compressor_tiny_inputs(lib):
+    import paper_1606_00519_gb300 as gmp
+    for data in (b"", b"x", b"xy", b"aaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaa", bytes(range(256)) * 3):
+        for de in (False, True):
+            s = gmp.compress(np.frombuffer(data, np.uint8), block_size=64, n_sub=4, window=32, de=de)
+            assert bytes(oracle.decompress(s)) == data
+
+
+def test_index_build_matches_header(lib):
+    import paper_1606_00519_gb300 as gmp
+    data = datagen.markov_text(300_000, seed=3, order=2)
+    s = oracle.compress(data, oracle.params(65536, 16, 8192))
+    idx, info = gmp.index_build(s)
+    assert info.n_blocks == 5 and info.orig_size == 300_000 and info.n_sub == 16
+    assert np.all(idx[:, 0] % 16 == 0)
+    assert list(idx[:, 2]) == [0, 65536, 131072, 196608, 262144]
+    assert list(idx[:, 3]) == [65536] * 4 + [300_000 - 4 * 65536]
+    assert np.all(idx[:-1, 0] + idx[:-1, 1] == idx[1:, 0])
+    assert 0 < info.max_block_seq <= 65536 // 3 + 1 and info.max_block_out == 65536
+
+
+def test_index_build_rejects_bad_headers(lib):
+    import paper_1606_00519_gb300 as gmp
+    s = oracle.compress(datagen.markov_text(50_000, seed=1), oracle.params(16384, 8, 4096))
+    bad = s.copy()
+    bad[0:4] = np.frombuffer(b"XXXX", np.uint8)
+    with pytest.raises(gmp.GmpError):
+        gmp.index_build(bad)
+    bad = s.copy()
+    bad[64:72] = np.frombuffer(np.uint64(3).tobytes(), np.uint8)  # misaligned block offset
+    with pytest.raises(gmp.GmpError):
+        gmp.index_build(bad)
+    with pytest.raises(gmp.GmpError):
+        gmp.index_build(s[:40])
+
+
+def test_decode_calls_fail_loudly_without_gpu(lib):
+    import torch
+    import paper_1606_00519_gb300 as gmp
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        gmp.Context()

@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA decoder (through the C ABI) against the CPU oracle,
+byte for byte, on every workload, both dependency modes, edge cases, and
+corrupt streams (which must give an error status, not a fault)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+KiB, MiB = 1 << 10, 1 << 20
+
+
+@pytest.fixture(scope="module")
+def gmp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1606_00519_gb300 import _native
+    _native.build()
+    import paper_1606_00519_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(gmp):
+    c = gmp.Context(max_block_out=256 * KiB, collect_stats=True)
+    yield c
+    c.close()
+
+
+def gpu_decode(gmp, ctx, stream):
+    ds = gmp.DeviceStream(stream)
+    out, status = ctx.decompress(ds)
+    return out.cpu().numpy(), status
+
+
+def check_stream(gmp, ctx, stream, data=None):
+    expect = oracle.decompress(stream)
+    got, status = gpu_decode(gmp, ctx, stream)
+    assert status == 0, gmp.STATUS_NAMES.get(status, status)
+    assert got.size == expect.size
+    if not np.array_equal(got, expect):
+        i = int(np.flatnonzero(got != expect)[0])
+        raise AssertionError(f"first differing byte {i} of {got.size}")
+    if data is not None:
+        assert np.array_equal(expect, data)
+
+
+@pytest.mark.parametrize("name", ["text1m", "text256m", "csv1g"])
+@pytest.mark.parametrize("mode", ["mrr", "de"])
+def test_oracle_streams(gmp, ctx, name, mode):
+    w = datagen.WORKLOADS[name]
+    data = w.data(5 * w.block_size + 4321)  # several blocks, ragged tail
+    s = oracle.compress(data, oracle.params(w.block_size, w.n_sub, w.window, de=(mode == "de")))
+    check_stream(gmp, ctx, s, data)
+
+
+@pytest.mark.parametrize("name", ["text1m", "text256m", "csv1g"])
+@pytest.mark.parametrize("mode", ["mrr", "de"])
+def test_product_streams(gmp, ctx, name, mode):
+    w = datagen.WORKLOADS[name]
+    data = w.data(9 * w.block_size + 99)
+    s = gmp.compress(data, w.block_size, w.n_sub, w.window, de=(mode == "de"))
+    check_stream(gmp, ctx, s, data)
+
+
+def test_text1m_full_config(gmp, ctx):
+    # the 1 MiB configuration end to end: 64 KiB blocks, 16 sub-blocks, MRR
+    w = datagen.WORKLOADS["text1m"]
+    data = w.data()
+    check_stream(gmp, ctx, oracle.compress(data, oracle.params(w.block_size, w.n_sub, w.window)), data)
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 8, 16, 32])
+def test_nesting_depth_streams_and_round_counts(gmp, ctx, m):
+    ts = datagen.nesting_tokens(seed=100 + m, m=m, n_inst=32 * 40)
+    s = oracle.encode_tokens(ts, oracle.params(block_size=256 * KiB, n_sub=16, window=32 * KiB))
+    ctx.stats_reset()
+    check_stream(gmp, ctx, s)
+    st = ctx.stats()
+    expect = oracle.mrr_rounds(ts.lit_len, ts.mlen, ts.off, ts.lits)
+    assert st["rounds"] == int(expect.sum())
+    assert st["max_rounds"] == 32 // m
+
+
+def test_de_streams_take_one_pass(gmp, ctx):
+    w = datagen.WORKLOADS["text256m"]
+    data = w.data(4 * w.block_size)
+    s = oracle.compress(data, oracle.params(w.block_size, w.n_sub, w.window, de=True))
+    ctx.stats_reset()
+    check_stream(gmp, ctx, s, data)
+    st = ctx.stats()
+    assert st["de_fallback_groups"] == 0 and st["max_rounds"] == 1 and st["groups"] > 0
+
+
+def test_wrong_de_flag_falls_back_to_mrr(gmp, ctx):
+    # an MRR stream flagged as DE: groups that break the DE property are
+    # resolved by MRR, so the output is still exact
+    w = datagen.WORKLOADS["csv1g"]
+    data = w.data(3 * w.block_size)
+    s = oracle.compress(data, oracle.params(w.block_size, w.n_sub, w.window, de=False))
+    s[6] |= 1
+    ctx.stats_reset()
+    got, status = gpu_decode(gmp, ctx, s)
+    assert status == 0 and np.array_equal(got, data)
+    assert ctx.stats()["de_fallback_groups"] > 0
+
+
+@pytest.mark.parametrize("n_sub", [1, 3, 32, 33, 64])
+def test_sub_block_counts(gmp, ctx, n_sub):
+    data = datagen.markov_text(700_000, seed=n_sub, order=3)
+    for de in (False, True):
+        s = oracle.compress(data, oracle.params(128 * KiB, n_sub, 16 * KiB, de=de))
+        check_stream(gmp, ctx, s, data)
+
+
+@pytest.mark.parametrize("size", [0, 1, 2, 15, 16, 17, 1000, 65535, 65536, 65537])
+def test_sizes(gmp, ctx, size):
+    data = datagen.csv_records(size, seed=size + 1) if size else np.zeros(0, np.uint8)
+    s = oracle.compress(data, oracle.params(64 * KiB, 16, 8 * KiB))
+    check_stream(gmp, ctx, s, data)
+
+
+def test_odd_block_sizes_and_small_windows(gmp, ctx):
+    data = datagen.markov_text(200_000, seed=8, order=2)
+    for bs, win, mm in [(1000, 1, 64), (4093, 4096, 3), (12345, 257, 17), (16, 8, 64)]:
+        p = oracle.params(bs, 4, win, max_match=mm)
+        check_stream(gmp, ctx, oracle.compress(data[:50_000], p), data[:50_000])
+
+
+def test_incompressible_and_degenerate_data(gmp, ctx):
+    rng = np.random.default_rng(5)
+    rnd = rng.integers(0, 256, 600_000).astype(np.uint8)      # long literal runs (slow path)
+    zeros = np.zeros(600_000, np.uint8)                         # distance-1 overlapping copies
+    two = np.tile(np.frombuffer(b"ab", np.uint8), 300_000)
+    for data in (rnd, zeros, two):
+        for de in (False, True):
+            s = oracle.compress(data, oracle.params(256 * KiB, 32, 32 * KiB, de=de))
+            check_stream(gmp, ctx, s, data)
+
+
+def test_unaligned_output_buffer(gmp, ctx):
+    import torch
+    data = datagen.markov_text(300_000, seed=4, order=3)
+    s = oracle.compress(data, oracle.params(64 * KiB, 16, 8 * KiB))
+    ds = gmp.DeviceStream(s)
+    base = torch.zeros(data.size + 64, dtype=torch.uint8, device="cuda")
+    out = base[3:3 + data.size]
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.decompress_into(ds, out, st)
+    assert int(st.item()) == 0
+    assert np.array_equal(out.cpu().numpy(), data)
+    assert int(base[:3].sum().item()) == 0 and int(base[3 + data.size:].sum().item()) == 0
+
+
+def test_output_guard_bytes_untouched(gmp, ctx):
+    import torch
+    data = datagen.csv_records(777_777, seed=9)
+    s = gmp.compress(data, 64 * KiB, 16, 8 * KiB)
+    ds = gmp.DeviceStream(s)
+    base = torch.full((data.size + 4096,), 0xA5, dtype=torch.uint8, device="cuda")
+    out = base[2048:2048 + data.size]
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.decompress_into(ds, out, st)
+    assert int(st.item()) == 0
+    b = base.cpu().numpy()
+    assert np.all(b[:2048] == 0xA5) and np.all(b[2048 + data.size:] == 0xA5)
+    assert np.array_equal(b[2048:2048 + data.size], data)
+
+
+def test_launch_shapes(gmp):
+    data = datagen.markov_text(2 * MiB, seed=12, order=3)
+    s = oracle.compress(data, oracle.params(128 * KiB, 32, 32 * KiB, de=True))
+    for wpc in (1, 2, 4, 8):
+        c = gmp.Context(max_block_out=128 * KiB, warps_per_cta=wpc)
+        got, status = gpu_decode(gmp, c, s)
+        assert status == 0 and np.array_equal(got, data)
+        c.close()
+
+
+def test_host_to_host_call(gmp, ctx):
+    data = datagen.csv_records(3 * MiB + 5, seed=21)
+    s = gmp.compress(data, 256 * KiB, 32, 32 * KiB, de=True)
+    out, status = ctx.decompress_host(s)
+    assert status == 0 and np.array_equal(out, data)
+
+
+# ---------------------------------------------------------------- corrupt input
+
+def _status(gmp, ctx, s):
+    return gpu_decode(gmp, ctx, s)[1]
+
+
+def _stream_for_corruption():
+    data = datagen.markov_text(5 * 64 * KiB, seed=31, order=2)
+    return data, oracle.compress(data, oracle.params(64 * KiB, 16, 8 * KiB))
+
+
+def _block_offset(s, b):
+    return int(s[64 + 8 * b:72 + 8 * b].view(np.uint64)[0])
+
+
+def test_corrupt_sub_block_size(gmp, ctx):
+    data, s = _stream_for_corruption()
+    bo = _block_offset(s, 1)
+    bad = s.copy()
+    v = bad[bo + 192:bo + 196].view(np.uint32)
+    v[0] -= 1  # sub-block 0 of block 1 claims one bit fewer
+    assert oracle.decompress_status(bad) == oracle.BITSTREAM
+    assert _status(gmp, ctx, bad) == oracle.BITSTREAM
+
+
+def test_corrupt_sub_block_out_bytes(gmp, ctx):
+    data, s = _stream_for_corruption()
+    bo = _block_offset(s, 2)
+    bad = s.copy()
+    v = bad[bo + 196:bo + 200].view(np.uint32)
+    v[0] += 1
+    assert oracle.decompress_status(bad) != oracle.OK
+    assert _status(gmp, ctx, bad) in (oracle.BAD_HEADER, oracle.OUTPUT_OVERRUN)
+
+
+def test_corrupt_code_lengths(gmp, ctx):
+    data, s = _stream_for_corruption()
+    bo = _block_offset(s, 0)
+    bad = s.copy()
+    bad[bo + 8 + ord("e") // 2] ^= 0x0F if ord("e") % 2 == 0 else 0xF0  # breaks Kraft equality
+    assert oracle.decompress_status(bad) == oracle.BAD_HEADER
+    assert _status(gmp, ctx, bad) == oracle.BAD_HEADER
+
+
+def test_window_smaller_than_distances(gmp, ctx):
+    data, s = _stream_for_corruption()
+    bad = s.copy()
+    bad[16:20] = np.frombuffer(np.uint32(2).tobytes(), np.uint8)  # header window = 2
+    assert oracle.decompress_status(bad) == oracle.BAD_OFFSET
+    assert _status(gmp, ctx, bad) == oracle.BAD_OFFSET
+
+
+def test_random_bit_flips_never_fault(gmp, ctx):
+    data, s = _stream_for_corruption()
+    rng = np.random.default_rng(77)
+    start = _block_offset(s, 0) + 200
+    agree = 0
+    for _ in range(60):
+        bad = s.copy()
+        i = int(rng.integers(start, s.size - 17))
+        bad[i] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        ost = oracle.decompress_status(bad)
+        got, st = gpu_decode(gmp, ctx, bad)
+        # both accept (and agree on the bytes) or both reject
+        assert (ost == 0) == (st == 0), (i, ost, st)
+        if ost == 0:
+            assert np.array_equal(got, oracle.decompress(bad))
+        agree += 1
+    assert agree == 60
+
+
+def test_capacity_status(gmp):
+    data = datagen.markov_text(600_000, seed=2, order=3)
+    s = oracle.compress(data, oracle.params(256 * KiB, 32, 32 * KiB))
+    c = gmp.Context(max_block_out=64 * KiB)
+    assert gpu_decode(gmp, c, s)[1] == 7
+    c.close()
