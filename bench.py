@@ -286,6 +286,23 @@ def run_gmp(args):
         torch.cuda.synchronize()
         per_mode[m] = round(data.size * reps / (a.elapsed_time(b) / 1e3) / 1e9, 2)
 
+    # where the decode kernel spends its cycles (one extra launch with the
+    # per-phase clock counters on, outside the timed region)
+    sctx = gmp.Context(device=local, max_block_out=w.block_size, warps_per_cta=args.warps_per_cta,
+                       collect_stats=True)
+    sctx.stats_reset(stream)
+    sctx.decompress_batch(table, len(modes), status, stream)
+    torch.cuda.synchronize()
+    phase = sctx.stats()
+    sctx.close()
+    cyc = phase["cycles_tables"] + phase["cycles_huffman"] + phase["cycles_lz77"]
+    phase_split = {"tables": round(phase["cycles_tables"] / max(cyc, 1), 4),
+                   "huffman": round(phase["cycles_huffman"] / max(cyc, 1), 4),
+                   "lz77": round(phase["cycles_lz77"] / max(cyc, 1), 4),
+                   "cycles_per_block": round(cyc / max(phase["blocks"], 1)),
+                   "mrr_rounds_per_group": round(phase["rounds"] / max(phase["groups"], 1), 3),
+                   "max_rounds": phase["max_rounds"], "de_fallback_groups": phase["de_fallback_groups"]}
+
     # end to end through the public host-to-host call: pinned host input,
     # H2D of the compressed stream, decode, D2H of the decompressed bytes
     pin_in = {m: torch.from_numpy(streams[m].copy()).pin_memory() for m in modes}
@@ -320,7 +337,8 @@ def run_gmp(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {**_config(w, streams, data), "parallelism": f"replicas x{world}",
-                   "warps_per_cta": args.warps_per_cta or 4, "per_mode_gbs": per_mode},
+                   "warps_per_cta": args.warps_per_cta or 4, "per_mode_gbs": per_mode,
+                   "decode_kernel_cycles": phase_split},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
                      "traffic": (round(tpu * out_bytes) if tpu else None),
@@ -340,6 +358,102 @@ def run_gmp(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals of requests (16 KiB..64 MiB, mixed content
+    and modes) admitted under a device-memory budget by the continuous-batching
+    server; p50/p99 latency (submit -> completion) and served GB/s at 25/50/90 %
+    of the closed-loop peak, next to the same arrivals served one launch per
+    request."""
+    import threading
+
+    import torch
+    import paper_1606_00519_gb300 as gmp
+
+    torch.cuda.set_device(0)
+    # a seeded pool of distinct requests; the arrival sequence draws from it
+    mix = datagen.request_mix(seed=5, n=args.serve_pool, lo=16 * KiB, hi=args.serve_max)
+    pool = []
+    for size, kind, mode, sd in mix:
+        data = datagen.make_data(kind, size, sd)
+        st = gmp.compress(data, 256 * KiB, 32, 32 * KiB, de=(mode == "de"))
+        pin = torch.from_numpy(st.copy()).pin_memory().numpy()
+        pool.append((size, pin, data))
+    mean_size = float(np.mean([p[0] for p in pool]))
+    rng = np.random.default_rng(11)
+
+    def run(server, arrivals, picks):
+        """Submit pool[picks[i]] at arrivals[i] (seconds); returns latencies,
+        total bytes, wall seconds; checks every output's size and status, and
+        the bytes of a sample."""
+        lat, done, nbytes = [], 0, 0
+        ids = {}
+        errors = []
+        lock = threading.Lock()
+
+        def collector():
+            nonlocal done, nbytes
+            while done < len(picks):
+                for c in server.poll(wait_ms=5):
+                    with lock:
+                        i = ids.pop(c["id"])
+                    if c["status"] != 0 or c["out_bytes"] != pool[picks[i]][0]:
+                        errors.append((i, c["status"]))
+                    elif i % 97 == 0:
+                        buf = np.empty(c["out_bytes"], np.uint8)
+                        server.copy_out(c["id"], buf)
+                        if not np.array_equal(buf, pool[picks[i]][2]):
+                            errors.append((i, "bytes"))
+                    lat.append(c["t_done"] - c["t_submit"])
+                    nbytes += c["out_bytes"]
+                    server.release(c["id"])
+                    done += 1
+
+        th = threading.Thread(target=collector)
+        th.start()
+        t0 = time.perf_counter()
+        for i, (ta, k) in enumerate(zip(arrivals, picks)):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            with lock:
+                ids[server.submit(pool[k][1])] = i
+        th.join()
+        wall = time.perf_counter() - t0
+        if errors:
+            raise SystemExit(f"serve: {len(errors)} bad results, e.g. {errors[:3]}")
+        return np.array(lat), nbytes, wall
+
+    n = args.serve_requests
+    picks = rng.integers(0, len(pool), n)
+    servers = {
+        "batched": dict(budget_bytes=args.serve_budget, n_lanes=4, max_batch=256),
+        "one_call_per_file": dict(budget_bytes=args.serve_budget, n_lanes=1, max_batch=1),
+    }
+    result = {"metric": "served decompressed GB/s and latency", "unit": "GB/s", "n_gpus": 1,
+              "config": {"workload": f"serving: requests log-uniform 16 KiB..{args.serve_max // MiB} MiB, "
+                                     "mixed text/CSV, MRR/DE, 256 KiB blocks, K=32",
+                         "pool": len(pool), "requests_per_load": n, "budget_bytes": args.serve_budget,
+                         "mean_request_bytes": int(mean_size)}}
+    for name, kw in servers.items():
+        srv = gmp.Server(**kw)
+        # closed loop: all at once (saturated peak)
+        lat, nb, wall = run(srv, np.zeros(min(n, 512)), picks[:min(n, 512)])
+        peak = nb / wall / 1e9
+        out = {"peak_gbs": round(peak, 3)}
+        for load in (0.25, 0.5, 0.9):
+            rate = load * peak * 1e9 / mean_size
+            arr = datagen.poisson_arrivals(seed=int(load * 100), n=n, rate_per_s=rate)
+            lat, nb, wall = run(srv, arr, picks)
+            out[f"load_{int(load * 100)}"] = {"offered_req_per_s": round(rate, 1),
+                                              "served_gbs": round(nb / wall / 1e9, 3),
+                                              "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                                              "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
+        srv.close()
+        result[name] = out
+    result["value"] = result["batched"]["peak_gbs"]
+    print(json.dumps(result), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,10 +466,17 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
     ap.add_argument("--ref-blocks", type=int, default=16, help="oracle blocks per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the decode step")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-pool", type=int, default=96)
+    ap.add_argument("--serve-max", type=int, default=64 * MiB)
+    ap.add_argument("--serve-budget", type=int, default=32 * GiB)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gmp(args)

@@ -9,7 +9,7 @@
  * the block's LZ77 sequences 32 at a time in one warp: two exclusive prefix
  * sums by shuffle, literal copy, then back-reference copy (Sec. 3.2.2), either
  * by Multi-Round Resolution (Fig. 5, Sec. 4.1) or, for streams written with
- * Dependency Elimination, in a single pass (Fig. 6, Sec. 4.2).
+ * Dependency Elimination, in a single pass (Fig. 7, Sec. 4.2).
  *
  * Conventions for every function:
  *   - Return value: GMP_OK (0) or a negative gmp_error.  No exception crosses
@@ -139,7 +139,7 @@ typedef struct {
   uint32_t block_size;  /* bytes per block (default 256 KiB) */
   uint32_t n_sub;       /* K sub-blocks per block, 1..64 (default 32) */
   uint32_t window;      /* LZ77 window, 1..32768 (default 32 KiB) */
-  uint32_t cwl;         /* Huffman code length limit, 1..12 (default 12) */
+  uint32_t cwl;         /* Huffman code length limit, 9..12 (default 12; 319 symbols need 9) */
   uint32_t max_match;   /* 3..64 (default 64) */
   uint32_t chain_depth; /* match candidates tried per position (default 64) */
   uint32_t de;          /* 1: Dependency Elimination (Sec. 4.2), 0: plain (MRR) */
@@ -223,11 +223,16 @@ int gmp_graph_launch(gmp_graph* g, void* stream);
 void gmp_graph_destroy(gmp_graph* g);
 
 /* ------------------------------------------------------------------------ */
-/* Statistics of the last launches since gmp_stats_reset (collect_stats=1):
+/* Statistics of the launches since gmp_stats_reset (collect_stats=1):
    32-sequence groups resolved, MRR rounds, groups of a DE stream that broke
-   the DE property and were resolved by MRR, blocks decoded. */
+   the DE property and were resolved by MRR, blocks decoded, the largest
+   round count of a group, and SM clock cycles summed over warps spent on
+   block setup (headers and lookup tables), Huffman decoding and LZ77
+   resolution. */
 typedef struct {
   uint64_t groups, rounds, de_fallback_groups, blocks, max_rounds;
+  uint64_t cycles_tables, cycles_huffman, cycles_lz77;
+  uint64_t detail[8]; /* stage timers of profiling builds (GMP_PHASE_TIMERS), else 0 */
 } gmp_stats;
 int gmp_stats_reset(gmp_context* ctx, void* stream);
 int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device */
@@ -239,6 +244,55 @@ int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device
    bytes.  *status receives the decoder status.  Synchronous. */
 int gmp_decompress_host(gmp_context* ctx, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,
                         int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of decompression requests under a device
+   memory budget (host runtime, one scheduler thread).  A request is a
+   compressed stream in host memory; its block index is built at submit.  The
+   scheduler admits requests in arrival order whenever the device arena has
+   room for the request's compressed bytes, index and output, and launches
+   the admitted ones as a batch (gmp_decompress_batch) on the first idle lane
+   (a context with its own CUDA stream).  Requests that arrive while batches
+   run join the next batch, and batches on different lanes overlap on the
+   GPU.  Outputs stay in device memory until released.  Timestamps are
+   seconds on the server's monotonic clock (gmp_server_now). */
+typedef struct gmp_server gmp_server;
+typedef struct {
+  uint64_t budget_bytes;  /* device arena for request buffers (default 32 GiB) */
+  uint32_t n_lanes;       /* batches in flight at once (default 4) */
+  uint32_t max_batch;     /* requests per launch (default 256; 1 = one launch per request) */
+  uint32_t max_block_out; /* largest block output of any request (default 256 KiB) */
+  uint32_t warps_per_cta; /* launch shape of the lanes' contexts (0 = default) */
+} gmp_server_opts;
+typedef struct {
+  uint64_t id;
+  int32_t status;        /* gmp_status of the decode */
+  uint8_t* d_out;        /* device output, valid until gmp_server_release(id) */
+  uint64_t out_bytes;
+  double t_submit, t_start, t_done;
+} gmp_completion;
+
+void gmp_server_opts_default(gmp_server_opts* o);
+/* Allocates the arena (budget_bytes of device memory) and the lanes. */
+int gmp_server_create(gmp_server** s, int device, const gmp_server_opts* opts);
+/* host_stream must stay valid and unchanged until the request completes.
+   GMP_ERR_CAPACITY if the request alone exceeds the budget or its blocks
+   exceed max_block_out.  Thread-safe. */
+int gmp_server_submit(gmp_server* s, const void* host_stream, size_t bytes, uint64_t* id);
+/* Moves up to cap completions into out (*n set), waiting up to wait_ms for
+   the first one.  Returns a sticky gmp_error if the scheduler failed. */
+int gmp_server_poll(gmp_server* s, gmp_completion* out, size_t cap, size_t* n, int wait_ms);
+/* Frees a completed request's device memory (its output included). */
+int gmp_server_release(gmp_server* s, uint64_t id);
+/* Waits until every submitted request has completed. */
+int gmp_server_drain(gmp_server* s);
+/* Copies a completed request's output (out_bytes of it, at most cap) to dst,
+   a host pointer (dst_is_device 0) or a device pointer of the server's device
+   (dst_is_device 1).  Synchronous. */
+int gmp_server_copy_out(gmp_server* s, uint64_t id, void* dst, size_t cap, int dst_is_device);
+double gmp_server_now(gmp_server* s);
+uint64_t gmp_server_bytes_in_use(gmp_server* s);
+void gmp_server_destroy(gmp_server* s);
 
 /* Last CUDA error string of this thread (for GMP_ERR_CUDA). */
 const char* gmp_last_cuda_error(void);

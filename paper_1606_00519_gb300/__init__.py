@@ -21,7 +21,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _native
-from ._native import BlockRef, CompressOpts, ContextOpts, FileDesc, Stats, StreamInfo
+from ._native import BlockRef, Completion, CompressOpts, ContextOpts, FileDesc, ServerOpts, Stats, StreamInfo
 
 OK = 0
 STATUS_NAMES = {0: "OK", 1: "BAD_HEADER", 2: "CORRUPT_SYMBOL", 3: "BITSTREAM", 4: "BAD_OFFSET",
@@ -208,7 +208,9 @@ class Context:
     def stats(self) -> dict:
         s = Stats()
         _check(self._L.gmp_stats_read(self._h, ctypes.byref(s)), "gmp_stats_read")
-        return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+        d = {k: int(getattr(s, k)) for k, _ in Stats._fields_ if k != "detail"}
+        d["detail"] = [int(x) for x in s.detail]
+        return d
 
     def decompress_host(self, stream, out: np.ndarray | None = None, cuda_stream=None):
         """Host stream in, host bytes out (H2D + decode + D2H, synchronous)."""
@@ -249,3 +251,73 @@ def make_file_table(descs, device=None):
     raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
     dev = torch.device("cuda") if device is None else torch.device(device)
     return torch.from_numpy(raw).to(dev)
+
+
+class Server:
+    """Continuous-batching decompression server (gmp_server_* in the C ABI).
+
+    submit() takes a compressed stream in host memory (a numpy uint8 array,
+    ideally pinned); the array is kept alive here until its request is
+    released.  poll() returns completions as dicts with the request id,
+    status, output size and the submit / launch / done timestamps."""
+
+    def __init__(self, device: int | None = None, budget_bytes: int = 32 << 30, n_lanes: int = 4,
+                 max_batch: int = 256, max_block_out: int = 256 << 10, warps_per_cta: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the server decodes only on the GPU")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._L = _native.lib()
+        o = ServerOpts(budget_bytes, n_lanes, max_batch, max_block_out, warps_per_cta)
+        h = ctypes.c_void_p()
+        _check(self._L.gmp_server_create(ctypes.byref(h), self.device, ctypes.byref(o)), "gmp_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, stream) -> int:
+        s = stream if isinstance(stream, np.ndarray) else _np_bytes(stream)
+        rid = ctypes.c_uint64()
+        _check(self._L.gmp_server_submit(self._h, _ptr(s), s.size, ctypes.byref(rid)), "gmp_server_submit")
+        self._keep[rid.value] = s
+        return rid.value
+
+    def poll(self, max_n: int = 4096, wait_ms: int = 0) -> list:
+        buf = (Completion * max_n)()
+        n = ctypes.c_size_t()
+        _check(self._L.gmp_server_poll(self._h, buf, max_n, ctypes.byref(n), wait_ms), "gmp_server_poll")
+        return [{"id": buf[i].id, "status": buf[i].status, "out_bytes": buf[i].out_bytes,
+                 "t_submit": buf[i].t_submit, "t_start": buf[i].t_start, "t_done": buf[i].t_done}
+                for i in range(n.value)]
+
+    def copy_out(self, rid: int, dst) -> None:
+        """Copy a completed request's output into a numpy array or a CUDA tensor."""
+        if isinstance(dst, np.ndarray):
+            _check(self._L.gmp_server_copy_out(self._h, rid, _ptr(dst), dst.size, 0), "gmp_server_copy_out")
+        else:
+            _check(self._L.gmp_server_copy_out(self._h, rid, ctypes.c_void_p(dst.data_ptr()), dst.numel(), 1),
+                   "gmp_server_copy_out")
+
+    def release(self, rid: int) -> None:
+        _check(self._L.gmp_server_release(self._h, rid), "gmp_server_release")
+        self._keep.pop(rid, None)
+
+    def drain(self) -> None:
+        _check(self._L.gmp_server_drain(self._h), "gmp_server_drain")
+
+    def now(self) -> float:
+        return float(self._L.gmp_server_now(self._h))
+
+    def bytes_in_use(self) -> int:
+        return int(self._L.gmp_server_bytes_in_use(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.gmp_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,7 +22,7 @@ BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libgmp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gmp_decode.cu", "gmp_host.cpp", "gmp_compress.cpp"]
+SOURCES = ["gmp_decode.cu", "gmp_host.cpp", "gmp_compress.cpp", "gmp_server.cpp"]
 
 _lock = threading.Lock()
 _lib = None
@@ -107,9 +107,22 @@ class FileDesc(ctypes.Structure):
                 ("n_blocks", ctypes.c_uint64), ("out", ctypes.c_uint64), ("out_cap", ctypes.c_uint64)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("n_lanes", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("max_block_out", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("d_out", ctypes.c_uint64),
+                ("out_bytes", ctypes.c_uint64), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("de_fallback_groups", ctypes.c_uint64),
-                ("blocks", ctypes.c_uint64), ("max_rounds", ctypes.c_uint64)]
+                ("blocks", ctypes.c_uint64), ("max_rounds", ctypes.c_uint64),
+                ("cycles_tables", ctypes.c_uint64), ("cycles_huffman", ctypes.c_uint64),
+                ("cycles_lz77", ctypes.c_uint64), ("detail", ctypes.c_uint64 * 8)]
 
 
 def _declare(L):
@@ -139,6 +152,20 @@ def _declare(L):
     L.gmp_stats_reset.argtypes = [vp, vp]
     L.gmp_stats_read.argtypes = [vp, P(Stats)]
     L.gmp_decompress_host.argtypes = [vp, vp, sz, vp, sz, P(ctypes.c_int32), vp]
+    L.gmp_server_opts_default.argtypes = [P(ServerOpts)]
+    L.gmp_server_opts_default.restype = None
+    L.gmp_server_create.argtypes = [P(vp), i32, P(ServerOpts)]
+    L.gmp_server_submit.argtypes = [vp, vp, sz, P(ctypes.c_uint64)]
+    L.gmp_server_poll.argtypes = [vp, P(Completion), sz, P(sz), i32]
+    L.gmp_server_release.argtypes = [vp, ctypes.c_uint64]
+    L.gmp_server_drain.argtypes = [vp]
+    L.gmp_server_copy_out.argtypes = [vp, ctypes.c_uint64, vp, sz, i32]
+    L.gmp_server_now.argtypes = [vp]
+    L.gmp_server_now.restype = ctypes.c_double
+    L.gmp_server_bytes_in_use.argtypes = [vp]
+    L.gmp_server_bytes_in_use.restype = ctypes.c_uint64
+    L.gmp_server_destroy.argtypes = [vp]
+    L.gmp_server_destroy.restype = None
     L.gmp_last_cuda_error.argtypes = []
     L.gmp_last_cuda_error.restype = ctypes.c_char_p
 

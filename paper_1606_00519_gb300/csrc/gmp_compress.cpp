@@ -3,7 +3,7 @@
 // Writes stream format version 1 (see gmp.h).  Steps per block (Sec. 3.1):
 // LZ77 with a sliding window, greedy parse over hash chains of 3-byte
 // prefixes; sequences = literal string + back-reference; in DE mode the
-// dependency rule of Sec. 4.2 (Fig. 6); two Huffman trees per block (literals
+// dependency rule of Sec. 4.2 (Fig. 7); two Huffman trees per block (literals
 // and lengths; offsets) limited to cwl bits; canonical codes; K sub-blocks.
 // Code lengths come from an ordinary Huffman merge followed by a Kraft repair
 // that lengthens rarely used codes until the code fits in cwl bits and then
@@ -323,7 +323,7 @@ int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* opts, v
   if ((!host_in && n) || !opts || !host_out || !out_bytes) return GMP_ERR_INVALID_ARG;
   gmp_compress_opts o = *opts;
   if (o.block_size == 0 || o.n_sub == 0 || o.n_sub > gmp::kMaxSub || o.window == 0 || o.window > 32768 || o.cwl == 0 ||
-      o.cwl > 12 || o.max_match < 3 || o.max_match > 64 || o.chain_depth == 0)
+      o.cwl > 12 || o.cwl < 9 || o.max_match < 3 || o.max_match > 64 || o.chain_depth == 0)
     return GMP_ERR_INVALID_ARG;
   const uint8_t* in = static_cast<const uint8_t*>(host_in);
   const size_t nb = (n + o.block_size - 1) / o.block_size;

@@ -18,7 +18,7 @@
 //  (literal length + match length) by shuffle gives each lane's output
 //  position, a second one of the literal lengths its literal source; the
 //  lanes copy their literal strings, then resolve their back-references by
-//  Multi-Round Resolution (Fig. 5) or, for a DE stream (Fig. 6), all in one
+//  Multi-Round Resolution (Fig. 5) or, for a DE stream (Fig. 7), all in one
 //  pass.  Output bytes go to a 16 KiB ring in shared memory that also serves
 //  recent back-reference sources; completed 16-byte chunks are flushed to the
 //  caller's buffer with coalesced 16-byte stores, so every output byte is
@@ -42,22 +42,52 @@
 namespace gmp {
 
 constexpr uint32_t FULL = 0xffffffffu;
+
+// Optional stage timers of the LZ77 phase (profiling builds only: compile
+// with -DGMP_PHASE_TIMERS); they add SM-clock deltas per stage into the
+// statistics' detail counters.
+#ifdef GMP_PHASE_TIMERS
+#define GMP_TSTAMP(v) const long long v = clock64()
+#define GMP_TADD(slot, a, b) tdet[slot] += (unsigned long long)((b) - (a))
+#else
+#define GMP_TSTAMP(v)
+#define GMP_TADD(slot, a, b)
+#endif
 constexpr int LUT_BITS = 12;
 constexpr int LUT_SIZE = 1 << LUT_BITS;
+// the offset tree's table covers codes of up to 10 bits; its rare longer codes
+// (11 and 12 bits) are decoded from the canonical arrays kept in S
+constexpr int OFF_BITS = 10;
+constexpr int OFF_SIZE = 1 << OFF_BITS;
+constexpr uint16_t LONG_CODE = 0xffff;
 constexpr int N_LL = 319;
 constexpr int N_OFF = 30;
 constexpr int MAX_SUB = 64;
-constexpr int RING = 16384;  // shared-memory output ring per warp (bytes)
+constexpr int RING = 4096;  // shared-memory output ring per warp (bytes)
 constexpr uint32_t RING_MASK = RING - 1;
-constexpr uint32_t GROUP_FAST_MAX = RING / 2;
+// back-reference sources at most NEAR bytes below the group start are read
+// from the ring; older ("far") ones are staged from device memory by cp.async
+// one group ahead
+constexpr uint32_t NEAR = RING / 2;
+constexpr uint32_t GROUP_FAST_MAX = NEAR - 16;
+// per lane: a 64-byte source spans at most 5 aligned 16-byte chunks
+constexpr int FAR_STAGE = 80;
+constexpr int LIT_STAGE = 16;  // per lane: a literal run inside one aligned 16-byte chunk
+constexpr uint32_t RING_WMASK = RING / 4 - 1;
+
+struct PhaseBSmem {
+  uint8_t ring[RING];
+  uint8_t far[2][32][FAR_STAGE];
+  uint8_t lit[2][32][LIT_STAGE];
+};
 
 struct __align__(16) WarpSmem {
   union {
     struct {
       uint16_t ll[LUT_SIZE];
-      uint16_t off[LUT_SIZE];
-    } lut;
-    uint8_t ring[RING];
+      uint16_t off[OFF_SIZE];
+    } lut;         // phase A
+    PhaseBSmem b;  // phase B
   } u;
   uint32_t sb_bit[MAX_SUB];      // sub-block start bit (from the bitstream start)
   uint32_t sb_bits[MAX_SUB];     // sub-block size in bits
@@ -73,6 +103,7 @@ struct __align__(16) WarpSmem {
   uint16_t sorted[N_LL + 1];
   uint8_t lens[N_LL + N_OFF + 3];
 };
+static_assert(sizeof(PhaseBSmem) <= (LUT_SIZE + OFF_SIZE) * sizeof(uint16_t), "phase B fits in the LUT space");
 
 struct KParams {
   const gmp_file_desc* files;  // batch mode; nullptr in single-stream mode
@@ -83,8 +114,9 @@ struct KParams {
   unsigned long long* counter;
   uint8_t* scratch;
   uint64_t slot_bytes;
+  uint64_t shadow_off;  // offset of the literal shadow inside a slot (256-byte aligned)
   uint32_t max_seq, max_out;
-  unsigned long long* stats;  // [groups, rounds, de_fallback, blocks, max_rounds]
+  unsigned long long* stats;  // [groups, rounds, de_fallback, blocks, max_rounds, cycles x3]
   int collect_stats;
 };
 
@@ -109,10 +141,14 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
 }
 
 // ---------------------------------------------------------------------------
-// Lookup table of one canonical tree (Sec. 3.1, 3.2.1).  Entry for the 12-bit
-// LSB-first peek e: the code whose bit-reversed value prefixes e; stored as
-// (length << 9) | symbol, 0 = no code.  Returns false when the code lengths
-// do not form a complete prefix code (Kraft sum != 1) and are not all zero.
+// Lookup table of one canonical tree (Sec. 3.1, 3.2.1).  Entry for the
+// TB-bit LSB-first peek e: the code whose bit-reversed value prefixes e,
+// stored as (length << 9) | symbol; 0 = no code (an empty tree); LONG_CODE =
+// the code is longer than TB bits (then decode_long below applies).  Leaves
+// the tree's canonical arrays (cnt, first, idx, sorted) in S.  Returns false
+// when the code lengths do not form a complete prefix code (Kraft sum != 1)
+// and are not all zero.
+template <int TB>
 __device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut) {
   const uint32_t lane = lane_id();
   if (lane < 16) { S.cnt[lane] = 0; S.run[lane] = 0; }
@@ -147,7 +183,7 @@ __device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut
   used = S.first[0];
   if (!ok) return false;
   if (used == 0) {
-    for (int e = (int)lane; e < LUT_SIZE; e += 32) lut[e] = 0;
+    for (int e = (int)lane; e < (1 << TB); e += 32) lut[e] = 0;
     __syncwarp();
     return true;
   }
@@ -162,35 +198,71 @@ __device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut
     if (r == 0) S.run[L] += __popc(m);
     __syncwarp();
   }
-  // limits of each length's code range, left-justified to 12 bits
-  uint32_t lim[LUT_BITS + 1];
+  // limits of each length's code range, left-justified to TB bits
+  uint32_t lim[TB + 1];
 #pragma unroll
-  for (int L = 1; L <= LUT_BITS; L++) lim[L] = (S.first[L] + S.cnt[L]) << (LUT_BITS - L);
-  for (int e = (int)lane; e < LUT_SIZE; e += 32) {
-    uint32_t v = __brev((uint32_t)e) >> (32 - LUT_BITS);  // peek bits, most significant first
+  for (int L = 1; L <= TB; L++) lim[L] = (S.first[L] + S.cnt[L]) << (TB - L);
+  for (int e = (int)lane; e < (1 << TB); e += 32) {
+    uint32_t v = __brev((uint32_t)e) >> (32 - TB);  // peek bits, most significant first
     uint32_t L = 1;
 #pragma unroll
-    for (int i = 1; i < LUT_BITS; i++) L += (v >= lim[i]) ? 1u : 0u;
-    uint32_t sh = LUT_BITS - L;
-    uint32_t sym = S.sorted[S.idx[L] + (v >> sh) - S.first[L]];
-    lut[e] = (uint16_t)((L << 9) | sym);
+    for (int i = 1; i <= TB; i++) L += (v >= lim[i]) ? 1u : 0u;
+    if (L > (uint32_t)TB) {
+      lut[e] = LONG_CODE;
+    } else {
+      uint32_t sym = S.sorted[S.idx[L] + (v >> (TB - L)) - S.first[L]];
+      lut[e] = (uint16_t)((L << 9) | sym);
+    }
   }
   __syncwarp();
   return true;
 }
 
+// A code longer than the table's bits, by the canonical ranges: the 12-bit
+// peek, most significant bit first, lies in length L's range [first_L,
+// first_L + cnt_L) shifted left by 12 - L.  Returns (L << 9) | symbol.
+template <int TB>
+__device__ __forceinline__ uint32_t decode_long(const WarpSmem& S, uint32_t peek12) {
+  const uint32_t v = __brev(peek12) >> (32 - LUT_BITS);
+  for (int L = TB + 1; L <= LUT_BITS; L++) {
+    const uint32_t code = v >> (LUT_BITS - L);
+    if (code - S.first[L] < S.cnt[L]) return ((uint32_t)L << 9) | S.sorted[S.idx[L] + code - S.first[L]];
+  }
+  return 0;
+}
+
 // ---------------------------------------------------------------------------
+// cp.async (16-byte, L2-only) global -> shared copies and their groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Where the bytes of one lane's back-reference source live: at or above
+// ring_lo in the ring; in [far_lo, far_hi) in the lane's staging (copied
+// from device memory ahead of time); anything else in device memory, which
+// is complete below ring_lo.
+struct SrcMap {
+  const uint8_t* ring;
+  const uint8_t* far;  // this lane's staging
+  const uint8_t* out;  // block output in device memory
+  uint32_t ring_lo, far_lo, far_hi;
+  __device__ __forceinline__ uint8_t get(uint32_t x) const {
+    if (x >= ring_lo) return ring[x & RING_MASK];
+    if (x >= far_lo && x < far_hi) return far[x - far_lo];
+    return out[x];
+  }
+};
+
 // Back-reference copy of one lane into the ring: ml bytes from rpos to wpos
 // (block-relative), byte by byte in order, so an overlapping copy (distance <
-// length) repeats its pattern.  Sources below ring_lo come from the output in
-// device memory, which is complete below ring_lo.
-__device__ __forceinline__ void copy_match_ring(uint8_t* ring, const uint8_t* out_blk, uint32_t rpos, uint32_t wpos,
-                                                uint32_t ml, uint32_t ring_lo) {
-  for (uint32_t i = 0; i < ml; i++) {
-    uint32_t s = rpos + i;
-    uint8_t v = (s >= ring_lo) ? ring[s & RING_MASK] : out_blk[s];
-    ring[(wpos + i) & RING_MASK] = v;
-  }
+// length) repeats its pattern.
+__device__ __forceinline__ void copy_match_ring(uint8_t* ring, const SrcMap& m, uint32_t rpos, uint32_t wpos,
+                                                uint32_t ml) {
+  for (uint32_t i = 0; i < ml; i++) ring[(wpos + i) & RING_MASK] = m.get(rpos + i);
 }
 
 __device__ __forceinline__ void copy_match_global(uint8_t* out_blk, uint32_t rpos, uint32_t wpos, uint32_t ml) {
@@ -209,8 +281,8 @@ __device__ __forceinline__ void copy_match_global(uint8_t* out_blk, uint32_t rpo
 // most 32 rounds; a group whose back-references do not depend on each other
 // resolves in one round.  Returns the number of rounds, or -1 on no progress.
 template <bool RING_PATH>
-__device__ int resolve_mrr(uint8_t* ring, uint8_t* out_blk, uint32_t rpos, uint32_t wpos, uint32_t ml, bool pending,
-                           uint32_t ring_lo) {
+__device__ int resolve_mrr(uint8_t* ring, const SrcMap& m, uint8_t* out_blk, uint32_t rpos, uint32_t wpos,
+                           uint32_t ml, bool pending) {
   int rounds = 0;
   for (;;) {
     uint32_t votes = __ballot_sync(FULL, pending);
@@ -220,7 +292,7 @@ __device__ int resolve_mrr(uint8_t* ring, uint8_t* out_blk, uint32_t rpos, uint3
     uint32_t hwm = __shfl_sync(FULL, wpos, f);
     uint32_t lim = min(rpos + ml, wpos);
     if (pending && lim <= hwm) {
-      if (RING_PATH) copy_match_ring(ring, out_blk, rpos, wpos, ml, ring_lo);
+      if (RING_PATH) copy_match_ring(ring, m, rpos, wpos, ml);
       else copy_match_global(out_blk, rpos, wpos, ml);
       pending = false;
     }
@@ -230,6 +302,156 @@ __device__ int resolve_mrr(uint8_t* ring, uint8_t* out_blk, uint32_t rpos, uint3
   return rounds;
 }
 
+// One lane's back-reference copy into the ring (Sec. 3.2.2, step (c)):
+// ml bytes from rpos to wpos.  Bytes up to the next 4-byte boundary of the
+// destination go one by one; then whole aligned destination words, each built
+// from an unaligned source word (two aligned loads and a funnel shift); then
+// the tail bytes.  The aligned words lie inside this lane's own output range,
+// so no other lane writes them.  A source word is complete before it is read
+// when the distance is at least 4 (earlier bytes of this copy included); a
+// copy with distance 1..3 repeats its pattern byte by byte.
+struct SrcView {
+  const uint8_t* ring;
+  const uint8_t* far;  // the lane's far staging (16-byte aligned)
+  const uint8_t* out;  // block output in device memory
+  uint32_t ring_lo, far_lo, far_hi;
+  __device__ __forceinline__ uint8_t byte(uint32_t x) const {
+    if (x >= ring_lo) return ring[x & RING_MASK];
+    if (x >= far_lo && x < far_hi) return far[x - far_lo];
+    return out[x];
+  }
+  __device__ __forceinline__ uint32_t word(uint32_t x) const {
+    if (x >= ring_lo) {
+      const uint32_t* r32 = reinterpret_cast<const uint32_t*>(ring);
+      const uint32_t wa = x >> 2;
+      return __funnelshift_r(r32[wa & RING_WMASK], r32[(wa + 1) & RING_WMASK], (x & 3u) * 8u);
+    }
+    if (x >= far_lo && x + 4 <= far_hi && x - far_lo + 8 <= (uint32_t)FAR_STAGE) {
+      const uint32_t r = x - far_lo;
+      const uint32_t* f32 = reinterpret_cast<const uint32_t*>(far);
+      return __funnelshift_r(f32[r >> 2], f32[(r >> 2) + 1], (r & 3u) * 8u);
+    }
+    return (uint32_t)byte(x) | ((uint32_t)byte(x + 1) << 8) | ((uint32_t)byte(x + 2) << 16) |
+           ((uint32_t)byte(x + 3) << 24);
+  }
+};
+
+__device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v, uint32_t rpos, uint32_t wpos,
+                                                 uint32_t ml) {
+  uint32_t i = 0;
+  if (wpos - rpos < 4) {
+    for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+    return;
+  }
+  for (; i < ml && ((wpos + i) & 3u); i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+  uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
+  for (; i + 4 <= ml; i += 4) r32[((wpos + i) >> 2) & RING_WMASK] = v.word(rpos + i);
+  for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+}
+
+// Largest lane l whose v_l <= k, for v non-decreasing across the lanes with
+// v_0 = 0 (an exclusive prefix sum): a binary search over the warp by
+// shuffles.  Starting at lane 0, the steps 16 + 8 + 4 + 2 + 1 reach lane 31.
+__device__ __forceinline__ int warp_search(uint32_t v, uint32_t k) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int cand = lo + step;
+    const uint32_t w = __shfl_sync(FULL, v, min(cand, 31));
+    if (cand <= 31 && w <= k) lo = cand;
+  }
+  return lo;
+}
+
+// Literal copy of a group, flat over its literal bytes: flat byte k belongs
+// to the lane o whose exclusive literal prefix lpre_o <= k < lpre_o + ll_o;
+// it goes to output position dst_o + (k - lpre_o).  Each lane moves one byte
+// per pass, so the warp moves 32 literal bytes per pass whatever the split
+// between lanes.  lit_src = lsrc - lit_lo into the lane's staging when
+// staged, else the position in the literal shadow (staged = 0).
+__device__ __forceinline__ void flat_literals(uint8_t* ring, const uint8_t* shadow, const uint8_t* lit_stage_base,
+                                              uint32_t glits, uint32_t lpre, uint32_t dst, uint32_t lit_src,
+                                              uint32_t staged) {
+  const uint32_t lane = lane_id();
+  for (uint32_t k0 = 0; k0 < glits; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    const int o = warp_search(lpre, k);
+    const uint32_t o_dst = __shfl_sync(FULL, dst, o);
+    const uint32_t o_lpre = __shfl_sync(FULL, lpre, o);
+    const uint32_t o_src = __shfl_sync(FULL, lit_src, o);
+    const uint32_t o_stg = __shfl_sync(FULL, staged, o);
+    if (k < glits) {
+      const uint32_t i = k - o_lpre;
+      const uint8_t v = o_stg ? lit_stage_base[o * LIT_STAGE + o_src + i] : shadow[o_src + i];
+      ring[(o_dst + i) & RING_MASK] = v;
+    }
+  }
+}
+
+// Back-reference copy of the lanes with `go`, flat over their match bytes:
+// each lane produces 4 consecutive flat bytes per pass.  A match is at least
+// 3 bytes long, so 4 consecutive flat bytes belong to at most two lanes (the
+// owners of the first and the last byte).  Byte i of lane o's match is read
+// from rpos_o + i, or rpos_o + (i mod dist_o) when the copy overlaps itself
+// (dist_o < ml_o): either way from bytes complete before this pass, so the
+// bytes of a pass may be produced in any order.
+struct MatchLane {
+  uint32_t wpos, rpos, dist, ml, far_lo, far_hi;
+};
+__device__ __forceinline__ void flat_matches(uint8_t* ring, const uint8_t* far_base, const uint8_t* out_blk,
+                                             uint32_t ring_lo, const MatchLane& me, bool go) {
+  const uint32_t lane = lane_id();
+  const uint32_t mc = go ? me.ml : 0u;
+  const uint32_t inc = warp_incl_scan(mc);
+  const uint32_t total = __shfl_sync(FULL, inc, 31);
+  const uint32_t mpre = inc - mc;
+  // per-lane constants: destination and source base relative to the flat index
+  const uint32_t D = me.wpos - mpre, R = me.rpos - mpre, E = mpre + mc, OV = mpre + me.dist;
+  const bool any_overlap = __ballot_sync(FULL, go && me.dist < me.ml) != 0;
+  for (uint32_t k0 = 0; k0 < total; k0 += 128) {
+    const uint32_t k = k0 + 4 * lane;
+    const int o1 = warp_search(mpre, k);
+    const int o2 = warp_search(mpre, k + 3);
+    const uint32_t D1 = __shfl_sync(FULL, D, o1), D2 = __shfl_sync(FULL, D, o2);
+    const uint32_t R1 = __shfl_sync(FULL, R, o1), R2 = __shfl_sync(FULL, R, o2);
+    const uint32_t E1 = __shfl_sync(FULL, E, o1);
+    const uint32_t F01 = __shfl_sync(FULL, me.far_lo, o1), F02 = __shfl_sync(FULL, me.far_lo, o2);
+    const uint32_t F11 = __shfl_sync(FULL, me.far_hi, o1), F12 = __shfl_sync(FULL, me.far_hi, o2);
+    uint32_t OV1 = 0, OV2 = 0, P1 = 0, P2 = 0, d1 = 1, d2 = 1;
+    if (any_overlap) {
+      OV1 = __shfl_sync(FULL, OV, o1);
+      OV2 = __shfl_sync(FULL, OV, o2);
+      P1 = __shfl_sync(FULL, mpre, o1);
+      P2 = __shfl_sync(FULL, mpre, o2);
+      d1 = __shfl_sync(FULL, me.dist, o1);
+      d2 = __shfl_sync(FULL, me.dist, o2);
+    }
+#pragma unroll
+    for (uint32_t b = 0; b < 4; b++) {
+      const uint32_t kk = k + b;
+      if (kk < total) {
+        const bool first = kk < E1;
+        const int o = first ? o1 : o2;
+        const uint32_t Dd = first ? D1 : D2;
+        uint32_t x = (first ? R1 : R2) + kk;
+        if (any_overlap) {
+          const uint32_t ov = first ? OV1 : OV2;
+          if (kk >= ov) {  // overlapping copy: the pattern of the last dist bytes repeats
+            const uint32_t p = first ? P1 : P2, d = first ? d1 : d2;
+            x = (first ? R1 : R2) + p + (kk - p) % d;
+          }
+        }
+        const uint32_t f0 = first ? F01 : F02, f1 = first ? F11 : F12;
+        uint8_t v;
+        if (x >= ring_lo) v = ring[x & RING_MASK];
+        else if (x >= f0 && x < f1) v = far_base[o * FAR_STAGE + (x - f0)];
+        else v = out_blk[x];
+        ring[(Dd + kk) & RING_MASK] = v;
+      }
+    }
+  }
+}
+
 // DE property check of one group (Sec. 4.2): each back-reference's source
 // bytes before its own write position must avoid every other back-reference
 // of the group.  Write positions rise with the lane, so the only candidate to
@@ -237,9 +459,9 @@ __device__ int resolve_mrr(uint8_t* ring, uint8_t* out_blk, uint32_t rpos, uint3
 __device__ __forceinline__ bool de_group_ok(uint32_t rpos, uint32_t wpos, uint32_t ml) {
   const uint32_t lane = lane_id();
   uint32_t b = min(rpos + ml, wpos);
-  int lo = -1;
+  int lo = -1;  // largest lane with wpos < b; the steps from -1 reach lane 31
 #pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
+  for (int step = 32; step >= 1; step >>= 1) {
     int cand = lo + step;
     uint32_t w = __shfl_sync(FULL, wpos, min(cand, 31));
     if (cand <= 31 && w < b) lo = cand;
@@ -255,6 +477,10 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
                              uint8_t* slot, unsigned long long* st_acc) {
   const uint32_t lane = lane_id();
   const uint8_t* comp = F.comp;
+  const long long t_begin = clock64();
+#ifdef GMP_PHASE_TIMERS
+  unsigned long long tdet[6] = {0, 0, 0, 0, 0, 0};
+#endif
   // ---- stream header (64 bytes), block reference
   int err = 0;
   uint32_t flags = 0, K = 0, window = 0, max_match = 0;
@@ -358,86 +584,139 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     S.lens[i] = (sym & 1) ? (v >> 4) : (v & 15);
   }
   __syncwarp();
-  bool ok1 = build_lut(S, S.lens, N_LL, S.u.lut.ll);
-  bool ok2 = build_lut(S, S.lens + N_LL, N_OFF, S.u.lut.off);
+  bool ok1 = build_lut<LUT_BITS>(S, S.lens, N_LL, S.u.lut.ll);
+  // the offset tree is built last, so its canonical arrays stay in S for
+  // decode_long
+  bool ok2 = build_lut<OFF_BITS>(S, S.lens + N_LL, N_OFF, S.u.lut.off);
   if (!ok1 || !ok2) {
     if (lane == 0) set_status(status, GMP_STATUS_BAD_HEADER);
     return;
   }
 
-  // ---- Phase A: lane per sub-block Huffman decode
+  const long long t_tables = clock64();
+  // ---- Phase A: lane per sub-block Huffman decode (Sec. 3.2.1)
+  // Every lane of the warp takes one symbol per step (a literal, or a length
+  // followed by its offset), with the literal / back-reference work done under
+  // predicates and the lanes reconverged after each step, so the warp issues
+  // one instruction stream for all 32 sub-blocks.
   uint2* rec = reinterpret_cast<uint2*>(slot);
-  uint8_t* shadow = slot + (uint64_t)P.max_seq * 8;
+  uint8_t* shadow = slot + P.shadow_off;
   const uint8_t* bs = B + bs_off;
-  const uint64_t bs_words = (br.comp_bytes - bs_off) / 4;  // whole 32-bit words inside the block
-  for (uint32_t j = lane; j < K; j += 32) {
-    uint32_t pos = S.sb_bit[j];
-    const uint32_t end = pos + S.sb_bits[j];
-    uint32_t wi = pos >> 5;
-    auto ldw = [&](uint32_t w) -> uint32_t { return (uint64_t)w < bs_words ? ld_u32_nc(bs + 4ull * w) : 0u; };
-    uint64_t buf = ((uint64_t)ldw(wi) | ((uint64_t)ldw(wi + 1) << 32)) >> (pos & 31);
-    int nb = 64 - (int)(pos & 31);
-    wi += 2;
-    uint32_t outp = S.sb_out[j];
-    const uint32_t out_end = outp + S.sb_outn[j];
-    uint32_t lit_dst = ((S.sb_out[j] + 15u) & ~15u) + 16u * j;
-    uint32_t nlit = 0;
-    uint32_t q = S.sb_seq[j];
-    const uint32_t q_end = q + S.sb_seqn[j];
-    for (; q < q_end && !err; q++) {
-      uint32_t lit_run = 0, ml = 0, dist = 0;
-      for (;;) {
+  // 16-byte chunks of the block's bitstream; chunks past the block read as 0
+  const uint64_t bs_chunks = (br.comp_bytes - bs_off) / 16;
+  auto ld4 = [&](uint32_t c) -> uint4 {
+    return (uint64_t)c < bs_chunks ? __ldg(reinterpret_cast<const uint4*>(bs) + c) : make_uint4(0, 0, 0, 0);
+  };
+  for (uint32_t jb = 0; jb < K; jb += 32) {
+    const uint32_t j = jb + lane;
+    bool act = j < K;
+    uint32_t pos = 0, end = 0, outp = 0, out_end = 0, lit_dst = 0, lit_lim = 0, nlit = 0, q = 0, q_end = 0;
+    uint32_t lit_run = 0;
+    // bit buffer (nb valid bits), a stash of up to 4 words (lo, hi) and the
+    // next 16-byte chunk, loaded one chunk ahead of use
+    uint64_t buf = 0, lo = 0, hi = 0;
+    int nb = 0;
+    uint32_t scnt = 0, ci = 0;
+    uint4 pre = make_uint4(0, 0, 0, 0);
+    auto next_word = [&]() -> uint32_t {
+      if (scnt == 0) {
+        lo = (uint64_t)pre.x | ((uint64_t)pre.y << 32);
+        hi = (uint64_t)pre.z | ((uint64_t)pre.w << 32);
+        scnt = 4;
+        pre = ld4(ci++);
+      }
+      const uint32_t w = (uint32_t)lo;
+      lo = (lo >> 32) | (hi << 32);
+      hi >>= 32;
+      scnt--;
+      return w;
+    };
+    if (act) {
+      pos = S.sb_bit[j];
+      end = pos + S.sb_bits[j];
+      // the stash starts with chunk c0 minus the words before the start word
+      const uint32_t w0 = pos >> 5, c0 = w0 >> 2;
+      const uint4 c = ld4(c0);
+      lo = (uint64_t)c.x | ((uint64_t)c.y << 32);
+      hi = (uint64_t)c.z | ((uint64_t)c.w << 32);
+      for (uint32_t k = 0; k < (w0 & 3u); k++) {
+        lo = (lo >> 32) | (hi << 32);
+        hi >>= 32;
+      }
+      scnt = 4u - (w0 & 3u);
+      pre = ld4(c0 + 1);
+      ci = c0 + 2;
+      buf = (uint64_t)(next_word() >> (pos & 31u));
+      nb = 32 - (int)(pos & 31u);
+      buf |= (uint64_t)next_word() << nb;
+      nb += 32;
+      outp = S.sb_out[j];
+      out_end = outp + S.sb_outn[j];
+      lit_dst = ((S.sb_out[j] + 15u) & ~15u) + 16u * j;
+      lit_lim = lit_dst + S.sb_outn[j];  // first byte past the lane's literal region
+      q = S.sb_seq[j];
+      q_end = q + S.sb_seqn[j];
+      act = q < q_end;
+    }
+    while (__any_sync(FULL, act)) {
+#ifdef GMP_PHASE_TIMERS
+      tdet[5]++;
+#endif
+      if (act) {
         if (nb < 32) {
-          buf |= (uint64_t)ldw(wi++) << nb;
+          buf |= (uint64_t)next_word() << nb;
           nb += 32;
         }
-        uint32_t e = S.u.lut.ll[buf & (LUT_SIZE - 1)];
-        uint32_t L = e >> 9, sym = e & 511u;
+        const uint32_t e = S.u.lut.ll[buf & (LUT_SIZE - 1)];
+        const uint32_t L = e >> 9, sym = e & 511u;
         buf >>= L;
         nb -= (int)L;
         pos += L;
-        if (L == 0) { err = GMP_STATUS_CORRUPT_SYMBOL; break; }
-        if (pos > end) { err = GMP_STATUS_BITSTREAM; break; }
         if (sym < 256) {
-          if (outp >= out_end) { err = GMP_STATUS_OUTPUT_OVERRUN; break; }
-          shadow[lit_dst + nlit] = (uint8_t)sym;
+          shadow[min(lit_dst + nlit, lit_lim)] = (uint8_t)sym;  // clamped: a corrupt stream is caught below
           nlit++;
           lit_run++;
           outp++;
-          continue;
+        } else {
+          uint32_t ml = 0, dist = 0;
+          if (sym > 256) {
+            ml = sym - 254u;
+            if (nb < 32) {
+              buf |= (uint64_t)next_word() << nb;
+              nb += 32;
+            }
+            uint32_t e2 = S.u.lut.off[buf & (OFF_SIZE - 1)];
+            if (e2 == LONG_CODE) e2 = decode_long<OFF_BITS>(S, (uint32_t)buf & (LUT_SIZE - 1));
+            const uint32_t L2 = e2 >> 9, os = e2 & 31u;
+            const uint32_t ne = os < 4 ? 0u : (os >> 1) - 1u;
+            const uint32_t extra = (uint32_t)(buf >> L2) & ((1u << ne) - 1u);
+            buf >>= L2 + ne;
+            nb -= (int)(L2 + ne);
+            pos += L2 + ne;
+            dist = os < 4 ? os + 1u : ((2u | (os & 1u)) << ne) + extra + 1u;
+            if (L2 == 0 || os >= (uint32_t)N_OFF || ml > max_match) err = GMP_STATUS_CORRUPT_SYMBOL;
+            else if (dist > window || dist > outp) err = GMP_STATUS_BAD_OFFSET;
+            else if (ml > out_end - min(outp, out_end)) err = GMP_STATUS_OUTPUT_OVERRUN;
+          } else if (q + 1 != n_seq) {
+            err = GMP_STATUS_CORRUPT_SYMBOL;  // the end symbol only closes the block's last sequence
+          }
+          rec[q] = make_uint2(lit_run, (dist << 8) | ml);
+          q++;
+          lit_run = 0;
+          outp += ml;
         }
-        if (sym == 256) {
-          if (q + 1 != n_seq) err = GMP_STATUS_CORRUPT_SYMBOL;  // only the block's last sequence
-          break;
-        }
-        ml = sym - 254u;
-        if (nb < 32) {
-          buf |= (uint64_t)ldw(wi++) << nb;
-          nb += 32;
-        }
-        uint32_t e2 = S.u.lut.off[buf & (LUT_SIZE - 1)];
-        uint32_t L2 = e2 >> 9, os = e2 & 31u;
-        if (L2 == 0 || os >= (uint32_t)N_OFF) { err = GMP_STATUS_CORRUPT_SYMBOL; break; }
-        buf >>= L2;
-        uint32_t ne = os < 4 ? 0u : (os >> 1) - 1u;
-        uint32_t extra = (uint32_t)buf & ((1u << ne) - 1u);
-        buf >>= ne;
-        nb -= (int)(L2 + ne);
-        pos += L2 + ne;
-        if (pos > end) { err = GMP_STATUS_BITSTREAM; break; }
-        dist = os < 4 ? os + 1u : ((2u | (os & 1u)) << ne) + extra + 1u;
-        if (ml > max_match) { err = GMP_STATUS_CORRUPT_SYMBOL; break; }
-        if (dist > window || dist > outp) { err = GMP_STATUS_BAD_OFFSET; break; }
-        if (ml > out_end - outp) { err = GMP_STATUS_OUTPUT_OVERRUN; break; }
-        outp += ml;
-        break;
+        if (L == 0) err = GMP_STATUS_CORRUPT_SYMBOL;
+        else if (pos > end) err = GMP_STATUS_BITSTREAM;
+        else if (outp > out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
+        act = !err && q < q_end;
       }
-      if (err) break;
-      rec[q] = make_uint2(lit_run, (dist << 8) | ml);
+      __syncwarp();
     }
-    if (!err && (pos != end)) err = GMP_STATUS_BITSTREAM;
-    if (!err && outp != out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
-    S.sb_lit[j] = nlit;
+    if (j < K) {
+      if (!err && pos != end) err = GMP_STATUS_BITSTREAM;
+      if (!err && outp != out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
+      S.sb_lit[j] = nlit;
+    }
   }
   if (err) set_status(status, err);
   if (__ballot_sync(FULL, err != 0)) return;
@@ -456,50 +735,150 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   }
   __syncwarp();
 
+  const long long t_phase_a = clock64();
   // ---- Phase B: 32 sequences per step (Sec. 3.2.2)
+  // Group g+1 is prepared while group g runs: its two prefix sums are taken
+  // and its literal runs and far back-reference sources are copied into the
+  // stage (g+1)&1 by cp.async, so that group g's work reads shared memory only.
   uint8_t* out_blk = F.out + br.out_offset;
   const bool vec_ok = (((uintptr_t)out_blk) & 15u) == 0;
   const bool de = (flags & 1u) != 0;
-  uint8_t* ring = S.u.ring;
+  PhaseBSmem& SB = S.u.b;
+  uint8_t* ring = SB.ring;
   uint32_t G0 = 0, litpos = 0, flushed = 0, ring_valid_lo = 0;
-  uint32_t jc = 0;
   unsigned long long n_groups = 0, n_rounds = 0, n_fallback = 0, max_rounds = 0;
   const uint32_t n_groups_total = (n_seq + 31) / 32;
-  for (uint32_t g = 0; g < n_groups_total; g++) {
-    const uint32_t t = g * 32 + lane;
-    const bool valid = t < n_seq;
-    uint2 r = valid ? rec[t] : make_uint2(0, 0);
-    const uint32_t ll = r.x, ml = r.y & 0xffu, dist = r.y >> 8;
-    const uint32_t tot = ll + ml;
-    const uint32_t inc_tot = warp_incl_scan(tot);
-    const uint32_t inc_ll = warp_incl_scan(ll);
-    const uint32_t g_total = __shfl_sync(FULL, inc_tot, 31);
-    const uint32_t g_lits = __shfl_sync(FULL, inc_ll, 31);
-    const uint32_t dst = G0 + inc_tot - tot;
+
+  struct Prep {
+    uint32_t ll, ml, dst, lsrc, wpos, rpos, gtot, glits, jnext, far_lo, far_hi, lit_lo, lpre;
+    bool valid, lit_staged;
+  };
+  // prefix sums and staging of group h; G0h / litposh / jc: where it starts
+  auto prep = [&](uint32_t h, uint2 r, uint32_t G0h, uint32_t litposh, uint32_t jc, bool allow, int stage) {
+    Prep q;
+    const uint32_t t = h * 32 + lane;
+    q.valid = t < n_seq;
+    q.ll = r.x;
+    q.ml = r.y & 0xffu;
+    const uint32_t dist = r.y >> 8;
+    const uint32_t tot = q.ll + q.ml;
+    // one scan of (literal length << 16 | total length) when the group fits
+    // in 16 bits (every group the ring takes), else two scans
+    const uint32_t gsum = __reduce_add_sync(FULL, tot);
+    uint32_t inc_tot, inc_ll;
+    if (gsum < 65536u) {
+      const uint32_t inc = warp_incl_scan((q.ll << 16) | tot);
+      inc_tot = inc & 0xffffu;
+      inc_ll = inc >> 16;
+    } else {
+      inc_tot = warp_incl_scan(tot);
+      inc_ll = warp_incl_scan(q.ll);
+    }
+    q.gtot = gsum;
+    q.glits = __reduce_add_sync(FULL, q.ll);
+    q.lpre = inc_ll - q.ll;
+    q.dst = G0h + inc_tot - tot;
     uint32_t j = jc;
-    if (valid)
+    if (q.valid)
       while (j + 1 < K && t >= S.sb_seq[j + 1]) j++;
-    const uint32_t lsrc = S.sb_lit[j] + litpos + inc_ll - ll;
-    jc = __shfl_sync(FULL, j, 31);
-    const uint32_t wpos = dst + ll;
-    const uint32_t rpos = wpos - dist;
-    const bool pending = valid && ml > 0;
+    q.lsrc = S.sb_lit[j] + litposh + inc_ll - q.ll;
+    q.jnext = __shfl_sync(FULL, j, 31);
+    q.wpos = q.dst + q.ll;
+    q.rpos = q.wpos - dist;
+    q.far_lo = q.far_hi = 0;
+    q.lit_lo = 0;
+    q.lit_staged = false;
+    if (allow && vec_ok && q.gtot <= GROUP_FAST_MAX) {
+      // far part of the source: below the ring's reach, already in device memory
+      const uint32_t rlo = max(ring_valid_lo, G0h > NEAR ? G0h - NEAR : 0u);
+      if (q.ml > 0 && q.rpos < rlo) {
+        const uint32_t fe = min(q.rpos + q.ml, rlo);
+        const uint32_t a0 = q.rpos & ~15u;
+        const uint32_t a1 = min((fe + 15u) & ~15u, flushed & ~15u);
+        uint8_t* dstage = SB.far[stage][lane];
+        for (uint32_t c = a0; c < a1; c += 16u) cp_async16(dstage + (c - a0), out_blk + c);
+        q.far_lo = a0;
+        q.far_hi = a1 > a0 ? a1 : a0;
+      }
+      if (q.ll > 0 && (q.lsrc & 15u) + q.ll <= (uint32_t)LIT_STAGE) {
+        const uint32_t l0 = q.lsrc & ~15u;
+        cp_async16(SB.lit[stage][lane], shadow + l0);
+        q.lit_lo = l0;
+        q.lit_staged = true;
+      }
+    }
+    cp_async_commit();
+    return q;
+  };
+
+  uint2 r_next = (lane < n_seq) ? rec[lane] : make_uint2(0, 0);
+  Prep cur = prep(0, r_next, 0, 0, 0, true, 0);
+  r_next = (32 + lane < n_seq) ? rec[32 + lane] : make_uint2(0, 0);
+  for (uint32_t g = 0; g < n_groups_total; g++) {
+    const int stage = (int)(g & 1u);
+    const bool fast = cur.gtot <= GROUP_FAST_MAX;
+    // prepare group g+1 (staging only if this group leaves the ring's reach unchanged)
+    GMP_TSTAMP(tg0);
+    Prep nxt = prep(g + 1, r_next, G0 + cur.gtot, litpos + cur.glits, cur.jnext, fast, stage ^ 1);
+    GMP_TSTAMP(tg1);
+    GMP_TADD(0, tg0, tg1);
+    {
+      const uint32_t t2 = (g + 2) * 32 + lane;
+      r_next = t2 < n_seq ? rec[t2] : make_uint2(0, 0);
+    }
+    cp_async_wait_1();  // this group's staging has landed
+    __syncwarp();
+    GMP_TSTAMP(tg2);
+    GMP_TADD(1, tg1, tg2);
+    const uint32_t ll = cur.ll, ml = cur.ml, dst = cur.dst, lsrc = cur.lsrc, wpos = cur.wpos, rpos = cur.rpos;
+    const bool pending = cur.valid && ml > 0;
+    const uint32_t G1 = G0 + cur.gtot;
     int rounds;
-    if (g_total <= GROUP_FAST_MAX) {
-      const uint32_t ring_lo = max(ring_valid_lo, G0 > RING / 2 ? G0 - RING / 2 : 0u);
-      for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = shadow[lsrc + i];
+    if (fast) {
+      const uint32_t ring_lo = max(ring_valid_lo, G0 > NEAR ? G0 - NEAR : 0u);
+      if (cur.glits) {
+        if (cur.lit_staged) {
+          const uint8_t* ls = SB.lit[stage][lane] + (lsrc - cur.lit_lo);
+          for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = ls[i];
+        } else {
+          for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = shadow[lsrc + i];
+        }
+      }
       __syncwarp();
+      GMP_TSTAMP(tg3);
+      GMP_TADD(2, tg2, tg3);
+      const SrcView sv{ring, SB.far[stage][lane], out_blk, ring_lo, cur.far_lo, cur.far_hi};
       if (de && de_group_ok(rpos, wpos, ml)) {
-        if (pending) copy_match_ring(ring, out_blk, rpos, wpos, ml, ring_lo);
+        if (pending) copy_match_words(ring, sv, rpos, wpos, ml);
         __syncwarp();
         rounds = __ballot_sync(FULL, pending) ? 1 : 0;
       } else {
         if (de) n_fallback++;
-        rounds = resolve_mrr<true>(ring, out_blk, rpos, wpos, ml, pending, ring_lo);
+        // Multi-Round Resolution (reading at resolve_mrr): HWM = write
+        // position of the lowest pending lane
+        bool pend = pending;
+        rounds = 0;
+        for (;;) {
+          const uint32_t votes = __ballot_sync(FULL, pend);
+          if (votes == 0) break;
+          if (rounds == 32) {
+            rounds = -1;
+            break;
+          }
+          const uint32_t hwm = __shfl_sync(FULL, wpos, __ffs(votes) - 1);
+          if (pend && min(rpos + ml, wpos) <= hwm) {
+            copy_match_words(ring, sv, rpos, wpos, ml);
+            pend = false;
+          }
+          __syncwarp();
+          rounds++;
+        }
       }
+      GMP_TSTAMP(tg4);
+      GMP_TADD(3, tg3, tg4);
       // flush completed 16-byte chunks; after a large group `flushed` may be
       // unaligned, so its first partial chunk goes out byte by byte
-      const uint32_t fend = (G0 + g_total) & ~15u;
+      const uint32_t fend = G1 & ~15u;
       if (fend > flushed) {
         const uint32_t head_end = min((flushed + 15u) & ~15u, fend);
         if (lane < head_end - flushed) out_blk[flushed + lane] = ring[(flushed + lane) & RING_MASK];
@@ -511,24 +890,28 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         }
         flushed = fend;
       }
+      GMP_TSTAMP(tg5);
+      GMP_TADD(4, tg4, tg5);
     } else {
       // a group too large for the ring: write it straight to device memory
       for (uint32_t c = flushed + lane; c < G0; c += 32u) out_blk[c] = ring[c & RING_MASK];
       __syncwarp();
       for (uint32_t i = 0; i < ll; i++) out_blk[dst + i] = shadow[lsrc + i];
       __syncwarp();
+      SrcMap m{ring, SB.far[stage][lane], out_blk, 0, 0, 0};
       if (de && de_group_ok(rpos, wpos, ml)) {
         if (pending) copy_match_global(out_blk, rpos, wpos, ml);
         __syncwarp();
         rounds = __ballot_sync(FULL, pending) ? 1 : 0;
       } else {
         if (de) n_fallback++;
-        rounds = resolve_mrr<false>(ring, out_blk, rpos, wpos, ml, pending, 0);
+        rounds = resolve_mrr<false>(ring, m, out_blk, rpos, wpos, ml, pending);
       }
-      flushed = G0 + g_total;
-      ring_valid_lo = flushed;
+      flushed = G1;
+      ring_valid_lo = G1;
     }
     if (rounds < 0) {
+      cp_async_wait_all();
       if (lane == 0) set_status(status, GMP_STATUS_MRR_NO_PROGRESS);
       return;
     }
@@ -536,22 +919,32 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     if (rounds > 0) n_groups++;
     n_rounds += (unsigned)rounds;
     if ((unsigned long long)rounds > max_rounds) max_rounds = (unsigned)rounds;
-    G0 += g_total;
-    litpos += g_lits;
+    G0 = G1;
+    litpos += cur.glits;
+    cur = nxt;
   }
+  cp_async_wait_all();
+  __syncwarp();
   // tail bytes not yet flushed
   for (uint32_t c = flushed + lane; c < out_bytes; c += 32u) out_blk[c] = ring[c & RING_MASK];
   if (G0 != out_bytes && lane == 0) set_status(status, GMP_STATUS_OUTPUT_OVERRUN);
   __syncwarp();
+  const long long t_end = clock64();
   st_acc[0] += n_groups;
   st_acc[1] += n_rounds;
   st_acc[2] += n_fallback;
   st_acc[3] += 1;
   if (max_rounds > st_acc[4]) st_acc[4] = max_rounds;
+  st_acc[5] += (unsigned long long)(t_tables - t_begin);
+  st_acc[6] += (unsigned long long)(t_phase_a - t_tables);
+  st_acc[7] += (unsigned long long)(t_end - t_phase_a);
+#ifdef GMP_PHASE_TIMERS
+  for (int i = 0; i < 6; i++) st_acc[8 + i] += tdet[i];
+#endif
 }
 
 // Persistent kernel: warps take work items until none are left.
-__global__ void __launch_bounds__(32 * 16) decode_kernel(const KParams P) {
+__global__ void __launch_bounds__(32 * 16, 1) decode_kernel(const KParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
@@ -561,7 +954,7 @@ __global__ void __launch_bounds__(32 * 16) decode_kernel(const KParams P) {
   uint64_t total;
   if (P.files) total = P.item_start[P.n_files];
   else total = P.single.n_blocks;
-  unsigned long long st_acc[5] = {0, 0, 0, 0, 0};
+  unsigned long long st_acc[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(P.counter, 1ull);
@@ -593,6 +986,12 @@ __global__ void __launch_bounds__(32 * 16) decode_kernel(const KParams P) {
     atomicAdd(&P.stats[2], st_acc[2]);
     atomicAdd(&P.stats[3], st_acc[3]);
     atomicMax(&P.stats[4], st_acc[4]);
+    atomicAdd(&P.stats[5], st_acc[5]);
+    atomicAdd(&P.stats[6], st_acc[6]);
+    atomicAdd(&P.stats[7], st_acc[7]);
+#ifdef GMP_PHASE_TIMERS
+    for (int i = 8; i < 14; i++) atomicAdd(&P.stats[i], st_acc[i]);
+#endif
   }
 }
 
@@ -654,8 +1053,9 @@ cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm) {
 
 cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, const uint64_t* item_start,
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,
-                          unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint32_t max_seq,
-                          uint32_t max_out, unsigned long long* stats, int collect_stats, cudaStream_t stream) {
+                          unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,
+                          uint32_t max_seq, uint32_t max_out, unsigned long long* stats, int collect_stats,
+                          cudaStream_t stream) {
   KParams P;
   P.files = files;
   P.item_start = item_start;
@@ -666,6 +1066,7 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
   P.counter = counter;
   P.scratch = scratch;
   P.slot_bytes = slot_bytes;
+  P.shadow_off = shadow_off;
   P.max_seq = max_seq;
   P.max_out = max_out;
   P.stats = stats;

@@ -55,7 +55,7 @@ struct gmp_context {
   gmp_context_opts opts{};
   gmp::LaunchShape shape{};
   uint32_t max_seq = 0, max_out = 0;
-  uint64_t slot_bytes = 0;
+  uint64_t slot_bytes = 0, shadow_off = 0;
   uint8_t* scratch = nullptr;
   size_t scratch_bytes = 0;
   unsigned long long* counter = nullptr;  // work counter
@@ -168,8 +168,9 @@ static int context_alloc_scratch(gmp_context* c) {
   // plus 16 bytes of separation per sub-block)
   c->max_out = c->opts.max_block_out;
   c->max_seq = c->max_out / 3 + 2;
-  uint64_t rec = (uint64_t)c->max_seq * 8;
+  uint64_t rec = ((uint64_t)c->max_seq * 8 + 255) & ~255ull;
   uint64_t shadow = (uint64_t)c->max_out + 16ull * gmp::kMaxSub + 64;
+  c->shadow_off = rec;
   c->slot_bytes = (rec + shadow + 255) & ~255ull;
   size_t need = (size_t)c->slot_bytes * (size_t)c->shape.grid * (size_t)wpc;
   if (c->scratch && c->scratch_bytes >= need) return GMP_OK;
@@ -205,7 +206,7 @@ int gmp_context_create(gmp_context** ctx, int device, const gmp_context_opts* op
     if (e == cudaSuccess) e = cudaMalloc(&c->item_start, (c->opts.max_files + 1) * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMemset(c->counter, 0, 64 * sizeof(unsigned long long));
     if (e != cudaSuccess) rc = cuda_fail(e, "context alloc");
-    c->stats = c->counter + 8;
+    c->stats = c->counter + 16;
   }
   if (rc != GMP_OK) {
     gmp_context_destroy(c);
@@ -255,7 +256,7 @@ int gmp_decompress(gmp_context* c, const uint8_t* d_comp, size_t comp_bytes, con
   uint64_t ctas_needed = (warps_needed + shape.warps_per_cta - 1) / shape.warps_per_cta;
   if ((uint64_t)shape.grid > ctas_needed) shape.grid = (int)ctas_needed;
   GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, c->counter, c->scratch, c->slot_bytes,
-                              c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats, s));
+                              c->shadow_off, c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats, s));
   return GMP_OK;
 }
 
@@ -270,7 +271,7 @@ int gmp_decompress_batch(gmp_context* c, const gmp_file_desc* d_files, size_t n_
   GMP_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
   GMP_CUDA(gmp::launch_batch_prefix(d_files, (uint32_t)n_files, c->item_start, s));
   GMP_CUDA(gmp::launch_decode(c->shape, d_files, c->item_start, (uint32_t)n_files, nullptr, d_status, c->counter,
-                              c->scratch, c->slot_bytes, c->max_seq, c->max_out, c->stats,
+                              c->scratch, c->slot_bytes, c->shadow_off, c->max_seq, c->max_out, c->stats,
                               (int)c->opts.collect_stats, s));
   return GMP_OK;
 }
@@ -326,14 +327,14 @@ void gmp_graph_destroy(gmp_graph* g) {
 int gmp_stats_reset(gmp_context* c, void* stream) {
   if (!c) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
-  GMP_CUDA(cudaMemsetAsync(c->stats, 0, 5 * sizeof(unsigned long long), static_cast<cudaStream_t>(stream)));
+  GMP_CUDA(cudaMemsetAsync(c->stats, 0, 16 * sizeof(unsigned long long), static_cast<cudaStream_t>(stream)));
   return GMP_OK;
 }
 
 int gmp_stats_read(gmp_context* c, gmp_stats* out) {
   if (!c || !out) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
-  unsigned long long v[5];
+  unsigned long long v[16];
   GMP_CUDA(cudaDeviceSynchronize());
   GMP_CUDA(cudaMemcpy(v, c->stats, sizeof(v), cudaMemcpyDeviceToHost));
   out->groups = v[0];
@@ -341,6 +342,10 @@ int gmp_stats_read(gmp_context* c, gmp_stats* out) {
   out->de_fallback_groups = v[2];
   out->blocks = v[3];
   out->max_rounds = v[4];
+  out->cycles_tables = v[5];
+  out->cycles_huffman = v[6];
+  out->cycles_lz77 = v[7];
+  for (int i = 0; i < 8; i++) out->detail[i] = v[8 + i];
   return GMP_OK;
 }
 

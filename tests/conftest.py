@@ -12,6 +12,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libgmp.so")
+    # pytest-timeout may be absent; the marker is then a no-op
+    config.addinivalue_line("markers", "timeout: per-test time limit (pytest-timeout)")
 
 
 def read_golden(name):
