@@ -11,7 +11,7 @@
  *   - block split, LZ77 with a sliding window and literal/back-reference
  *     tokens grouped into sequences (Sec. 2.1, Fig. 1; Sec. 3.1; Sec. 3.2.2
  *     "sequence"), greedy parse with trigram hash chains;
- *   - Dependency Elimination, the modified LZ77 of Fig. 6 (Sec. 4.2): per
+ *   - Dependency Elimination, the modified LZ77 of Fig. 7 (Sec. 4.2): per
  *     group of 32 sequences, matches are looked for below warpHWM = the
  *     position where the group started;
  *   - two Huffman trees per block (literals + match lengths, and offsets;
@@ -294,8 +294,8 @@ static void seq_free(seqbuf* s) { free(s->lit_len); free(s->mlen); free(s->off);
    Sec. 4.2), at most chain_depth candidates per position, longest match in
    [min_match, max_match], distance <= window and <= position in the block;
    the nearest candidate wins ties.
-   DE mode (Fig. 6, Sec. 4.2): per group of 32 sequences, warpHWM is the
-   position where the group started.  Read literally, Fig. 6 never finds a
+   DE mode (Fig. 7, Sec. 4.2): per group of 32 sequences, warpHWM is the
+   position where the group started.  Read literally, Fig. 7 never finds a
    match in a block's first group (warpHWM = 0 and a group only closes after
    32 matches), so this oracle takes the reading that matches what the DE
    decoder has finished before the group's copies run: every byte below
