@@ -22,7 +22,7 @@ BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libgmp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gmp_decode.cu", "gmp_host.cpp", "gmp_compress.cpp", "gmp_server.cpp"]
+SOURCES = ["gmp_decode.cu", "gmp_host.cpp", "gmp_compress.cpp", "gmp_server.cpp", "gmp_noalloc.cu"]
 
 _lock = threading.Lock()
 _lib = None
@@ -166,6 +166,9 @@ def _declare(L):
     L.gmp_server_bytes_in_use.restype = ctypes.c_uint64
     L.gmp_server_destroy.argtypes = [vp]
     L.gmp_server_destroy.restype = None
+    L.gmp_decompress_noalloc.argtypes = [vp, sz, vp, sz, ctypes.c_uint32, vp, sz, vp, vp]
+    L.gmp_noalloc_limits.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint64)]
+    L.gmp_noalloc_limits.restype = None
     L.gmp_last_cuda_error.argtypes = []
     L.gmp_last_cuda_error.restype = ctypes.c_char_p
 
