@@ -56,9 +56,10 @@
  *   an offset symbol.  Offset symbol for distance d, v = d - 1: v < 4 gives
  *   symbol v; otherwise, with k = floor(log2 v), symbol 2k + bit (k-1) of v,
  *   followed by k-1 extra bits holding v mod 2^(k-1), LSB-first.
- *   Sub-blocks: a block's n_seq sequences are cut into K runs of
- *   ceil(n_seq/K) sequences (trailing runs may be short or empty).  A
- *   sequence is a literal string followed by one back-reference (Sec. 3.2.2).
+ *   Sub-blocks: a block's n_seq sequences are cut into K consecutive runs of
+ *   whole sequences (runs may be empty); the decoder accepts any such split.
+ *   gmp_compress makes the runs equal in decoding steps (literals + sequences).
+ *   A sequence is a literal string followed by one back-reference (Sec. 3.2.2).
  *   Canonical codes (Sec. 3.1): codes of each length are consecutive in
  *   symbol order; the first code of length L is (first(L-1) + count(L-1)) << 1.
  *   DE flag: every back-reference of a 32-sequence group (numbered from the

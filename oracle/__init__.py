@@ -75,7 +75,7 @@ class Report(ctypes.Structure):
                 ("de_strong_ok", ctypes.c_int32), ("de_weak_ok", ctypes.c_int32), ("mrr_ok", ctypes.c_int32),
                 ("groups", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("max_rounds", ctypes.c_uint64),
                 ("copies", ctypes.c_uint64), ("round_hist", ctypes.c_uint64 * 34),
-                ("first_error", ctypes.c_int32)]
+                ("first_error", ctypes.c_int32), ("subblocks_even", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "round_hist"}

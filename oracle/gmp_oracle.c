@@ -891,12 +891,14 @@ typedef struct {
   uint64_t groups, rounds, max_rounds, copies;
   uint64_t round_hist[34];
   int32_t first_error;
+  int32_t subblocks_even;
 } orc_report;
 
 int orc_validate(const uint8_t* s, uint64_t len, orc_report* R) {
   memset(R, 0, sizeof(*R));
   R->kraft_ok = R->lengths_ok = R->offsets_ok = R->blocks_ok = R->subblocks_ok = 1;
   R->de_strong_ok = R->de_weak_ok = R->mrr_ok = 1;
+  R->subblocks_even = 1;
   orc_info I;
   int rc = orc_stream_info(s, len, &I);
   if (rc) { R->first_error = rc; return rc; }
@@ -923,13 +925,16 @@ int orc_validate(const uint8_t* s, uint64_t len, orc_report* R) {
       R->first_error = rc;
       return rc;
     }
-    /* sub-block split of c5: ceil(n_seq / K) sequences each */
+    /* The format only fixes that the K sub-blocks are consecutive runs of
+       whole sequences whose stored sizes match their bits (block_tokens
+       checked that).  Whether the runs are the even split of c5, ceil(n_seq
+       / K) sequences each (this oracle's own choice), is reported apart. */
     {
       uint64_t per = (S.n + I.n_sub - 1) / I.n_sub, left = S.n;
       for (uint32_t j = 0; j < I.n_sub; j++) {
         uint32_t ns = get32(B + BLK_FIXED + 12 * j + 8);
         uint64_t want = left < per ? left : per;
-        if (ns != want) R->subblocks_ok = 0;
+        if (ns != want) R->subblocks_even = 0;
         left -= want;
       }
     }

@@ -264,10 +264,19 @@ void encode_block(const uint8_t* in, uint32_t n, const std::vector<Seq>& seqs, c
   for (uint32_t s = 0; s < gmp::kLitLenSyms; s++) blk[8 + s / 2] |= (uint8_t)(l1[s] << (4 * (s & 1)));
   for (uint32_t s = 0; s < gmp::kOffsetSyms; s++) blk[168 + s / 2] |= (uint8_t)(l2[s] << (4 * (s & 1)));
   BitSink bs(blk);
-  const size_t per = (seqs.size() + K - 1) / K;
+  // Sub-blocks of equal decoding work: a lane decodes one literal/length
+  // symbol per step, so sequence q costs lit_len + 1 steps; sub-block j ends
+  // where the running cost first reaches (j + 1) / K of the block's total.
+  // (A block's first sequences carry most of its literals, since its window
+  // starts empty, so an even split by sequence count is uneven in work.)
+  uint64_t total_cost = 0;
+  for (const Seq& q : seqs) total_cost += q.lit_len + 1ull;
+  uint64_t run_cost = 0;
   size_t qi = 0;
   for (uint32_t j = 0; j < K; j++) {
-    const size_t qe = std::min(seqs.size(), qi + per);
+    const uint64_t target = total_cost * (j + 1) / K;
+    size_t qe = qi;
+    while (qe < seqs.size() && (run_cost < target || j + 1 == K)) run_cost += seqs[qe++].lit_len + 1ull;
     const uint64_t b0 = bs.bits();
     uint32_t outn = 0;
     const uint32_t nseq = (uint32_t)(qe - qi);

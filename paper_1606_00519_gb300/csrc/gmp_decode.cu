@@ -72,13 +72,15 @@ constexpr uint32_t NEAR = RING / 2;
 constexpr uint32_t GROUP_FAST_MAX = NEAR - 16;
 // per lane: a 64-byte source spans at most 5 aligned 16-byte chunks
 constexpr int FAR_STAGE = 80;
-constexpr int LIT_STAGE = 16;  // per lane: a literal run inside one aligned 16-byte chunk
+// per group: the group's literal bytes when they are one contiguous run of
+// the shadow (all in one sub-block) and fit, with alignment, in 32 chunks
+constexpr int LIT_STAGE = 512;
 constexpr uint32_t RING_WMASK = RING / 4 - 1;
 
 struct PhaseBSmem {
   uint8_t ring[RING];
   uint8_t far[2][32][FAR_STAGE];
-  uint8_t lit[2][32][LIT_STAGE];
+  uint8_t lit[2][LIT_STAGE];
 };
 
 struct __align__(16) WarpSmem {
@@ -339,13 +341,29 @@ struct SrcView {
 __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v, uint32_t rpos, uint32_t wpos,
                                                  uint32_t ml) {
   uint32_t i = 0;
-  if (wpos - rpos < 4) {
+  const bool in_ring = rpos >= v.ring_lo;                                      // whole source in the ring
+  const bool in_far = !in_ring && rpos >= v.far_lo && rpos + ml <= v.far_hi;   // whole source staged
+  if (wpos - rpos < 4 || !(in_ring || in_far)) {
     for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
     return;
   }
   for (; i < ml && ((wpos + i) & 3u); i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
   uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
-  for (; i + 4 <= ml; i += 4) r32[((wpos + i) >> 2) & RING_WMASK] = v.word(rpos + i);
+  if (in_ring) {
+    for (; i + 4 <= ml; i += 4) {
+      const uint32_t x = rpos + i, wa = x >> 2;
+      r32[((wpos + i) >> 2) & RING_WMASK] =
+          __funnelshift_r(r32[wa & RING_WMASK], r32[(wa + 1) & RING_WMASK], (x & 3u) * 8u);
+    }
+  } else {
+    // staged source: a plain array (the pair read may run up to one word
+    // past the lane's slot, into other staging; those bytes are discarded)
+    const uint32_t* f32 = reinterpret_cast<const uint32_t*>(v.far);
+    for (; i + 4 <= ml; i += 4) {
+      const uint32_t r = rpos - v.far_lo + i;
+      r32[((wpos + i) >> 2) & RING_WMASK] = __funnelshift_r(f32[r >> 2], f32[(r >> 2) + 1], (r & 3u) * 8u);
+    }
+  }
   for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
 }
 
@@ -800,9 +818,17 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         q.far_lo = a0;
         q.far_hi = a1 > a0 ? a1 : a0;
       }
-      if (q.ll > 0 && (q.lsrc & 15u) + q.ll <= (uint32_t)LIT_STAGE) {
-        const uint32_t l0 = q.lsrc & ~15u;
-        cp_async16(SB.lit[stage][lane], shadow + l0);
+    }
+    // the group's literals, one contiguous run of the shadow when they all
+    // belong to one sub-block: lane i stages the run's i-th 16-byte chunk
+    if (allow && q.glits > 0 && q.gtot <= GROUP_FAST_MAX) {
+      const uint32_t last = 31u - (uint32_t)__clz(__ballot_sync(FULL, q.valid) | 1u);
+      const uint32_t j_first = __shfl_sync(FULL, j, 0), j_last = __shfl_sync(FULL, j, last);
+      const uint32_t base = __shfl_sync(FULL, q.lsrc, 0);
+      const uint32_t l0 = base & ~15u, l1 = (base + q.glits + 15u) & ~15u;
+      if (j_first == j_last && l1 - l0 <= (uint32_t)LIT_STAGE) {
+        const uint32_t c = l0 + 16u * lane;
+        if (c < l1) cp_async16(SB.lit[stage] + (c - l0), shadow + c);
         q.lit_lo = l0;
         q.lit_staged = true;
       }
@@ -838,7 +864,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       const uint32_t ring_lo = max(ring_valid_lo, G0 > NEAR ? G0 - NEAR : 0u);
       if (cur.glits) {
         if (cur.lit_staged) {
-          const uint8_t* ls = SB.lit[stage][lane] + (lsrc - cur.lit_lo);
+          const uint8_t* ls = SB.lit[stage] + (lsrc - cur.lit_lo);
           for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = ls[i];
         } else {
           for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = shadow[lsrc + i];

@@ -28,7 +28,7 @@ def test_every_tiny_input(alphabet, max_len, block_size):
             assert bytes(oracle.decompress(s)) == data
             r = oracle.validate(s)
             assert r["rc"] == 0 and r["offsets_ok"] and r["kraft_ok"] and r["blocks_ok"] and r["mrr_ok"]
-            assert r["subblocks_ok"]
+            assert r["subblocks_ok"] and r["subblocks_even"]
             if p.de:
                 assert r["de_weak_ok"], data
             n_matches += r["n_matches"]

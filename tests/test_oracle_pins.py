@@ -234,7 +234,7 @@ def test_roundtrip_and_validators(name):
         assert np.array_equal(oracle.decompress(s), data)
         r = oracle.validate(s)
         assert r["rc"] == 0
-        for k in ("kraft_ok", "lengths_ok", "offsets_ok", "blocks_ok", "subblocks_ok", "mrr_ok"):
+        for k in ("kraft_ok", "lengths_ok", "offsets_ok", "blocks_ok", "subblocks_ok", "subblocks_even", "mrr_ok"):
             assert r[k] == 1, k
         assert r["n_blocks"] == 4
         if mode == "de":
