@@ -25,7 +25,7 @@
 //  written to device memory once.
 //
 // MRR reading (the printed algorithm is ambiguous, see the comment at
-// resolve_mrr): HWM = write position of the lowest pending lane; a lane may
+// resolve_mrr_global): HWM = write position of the lowest pending lane; a lane may
 // copy once min(read_pos + length, write_pos) <= HWM.
 //
 // Every read of the compressed stream is bounds-checked; every loop over
@@ -243,30 +243,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Where the bytes of one lane's back-reference source live: at or above
-// ring_lo in the ring; in [far_lo, far_hi) in the lane's staging (copied
-// from device memory ahead of time); anything else in device memory, which
-// is complete below ring_lo.
-struct SrcMap {
-  const uint8_t* ring;
-  const uint8_t* far;  // this lane's staging
-  const uint8_t* out;  // block output in device memory
-  uint32_t ring_lo, far_lo, far_hi;
-  __device__ __forceinline__ uint8_t get(uint32_t x) const {
-    if (x >= ring_lo) return ring[x & RING_MASK];
-    if (x >= far_lo && x < far_hi) return far[x - far_lo];
-    return out[x];
-  }
-};
-
-// Back-reference copy of one lane into the ring: ml bytes from rpos to wpos
-// (block-relative), byte by byte in order, so an overlapping copy (distance <
-// length) repeats its pattern.
-__device__ __forceinline__ void copy_match_ring(uint8_t* ring, const SrcMap& m, uint32_t rpos, uint32_t wpos,
-                                                uint32_t ml) {
-  for (uint32_t i = 0; i < ml; i++) ring[(wpos + i) & RING_MASK] = m.get(rpos + i);
-}
-
 __device__ __forceinline__ void copy_match_global(uint8_t* out_blk, uint32_t rpos, uint32_t wpos, uint32_t ml) {
   for (uint32_t i = 0; i < ml; i++) out_blk[wpos + i] = out_blk[rpos + i];
 }
@@ -282,9 +258,7 @@ __device__ __forceinline__ void copy_match_global(uint8_t* out_blk, uint32_t rpo
 // qualifies, so every round resolves at least one lane and a group needs at
 // most 32 rounds; a group whose back-references do not depend on each other
 // resolves in one round.  Returns the number of rounds, or -1 on no progress.
-template <bool RING_PATH>
-__device__ int resolve_mrr(uint8_t* ring, const SrcMap& m, uint8_t* out_blk, uint32_t rpos, uint32_t wpos,
-                           uint32_t ml, bool pending) {
+__device__ int resolve_mrr_global(uint8_t* out_blk, uint32_t rpos, uint32_t wpos, uint32_t ml, bool pending) {
   int rounds = 0;
   for (;;) {
     uint32_t votes = __ballot_sync(FULL, pending);
@@ -294,8 +268,7 @@ __device__ int resolve_mrr(uint8_t* ring, const SrcMap& m, uint8_t* out_blk, uin
     uint32_t hwm = __shfl_sync(FULL, wpos, f);
     uint32_t lim = min(rpos + ml, wpos);
     if (pending && lim <= hwm) {
-      if (RING_PATH) copy_match_ring(ring, m, rpos, wpos, ml);
-      else copy_match_global(out_blk, rpos, wpos, ml);
+      copy_match_global(out_blk, rpos, wpos, ml);
       pending = false;
     }
     __syncwarp();
@@ -365,109 +338,6 @@ __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v
     }
   }
   for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
-}
-
-// Largest lane l whose v_l <= k, for v non-decreasing across the lanes with
-// v_0 = 0 (an exclusive prefix sum): a binary search over the warp by
-// shuffles.  Starting at lane 0, the steps 16 + 8 + 4 + 2 + 1 reach lane 31.
-__device__ __forceinline__ int warp_search(uint32_t v, uint32_t k) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const int cand = lo + step;
-    const uint32_t w = __shfl_sync(FULL, v, min(cand, 31));
-    if (cand <= 31 && w <= k) lo = cand;
-  }
-  return lo;
-}
-
-// Literal copy of a group, flat over its literal bytes: flat byte k belongs
-// to the lane o whose exclusive literal prefix lpre_o <= k < lpre_o + ll_o;
-// it goes to output position dst_o + (k - lpre_o).  Each lane moves one byte
-// per pass, so the warp moves 32 literal bytes per pass whatever the split
-// between lanes.  lit_src = lsrc - lit_lo into the lane's staging when
-// staged, else the position in the literal shadow (staged = 0).
-__device__ __forceinline__ void flat_literals(uint8_t* ring, const uint8_t* shadow, const uint8_t* lit_stage_base,
-                                              uint32_t glits, uint32_t lpre, uint32_t dst, uint32_t lit_src,
-                                              uint32_t staged) {
-  const uint32_t lane = lane_id();
-  for (uint32_t k0 = 0; k0 < glits; k0 += 32) {
-    const uint32_t k = k0 + lane;
-    const int o = warp_search(lpre, k);
-    const uint32_t o_dst = __shfl_sync(FULL, dst, o);
-    const uint32_t o_lpre = __shfl_sync(FULL, lpre, o);
-    const uint32_t o_src = __shfl_sync(FULL, lit_src, o);
-    const uint32_t o_stg = __shfl_sync(FULL, staged, o);
-    if (k < glits) {
-      const uint32_t i = k - o_lpre;
-      const uint8_t v = o_stg ? lit_stage_base[o * LIT_STAGE + o_src + i] : shadow[o_src + i];
-      ring[(o_dst + i) & RING_MASK] = v;
-    }
-  }
-}
-
-// Back-reference copy of the lanes with `go`, flat over their match bytes:
-// each lane produces 4 consecutive flat bytes per pass.  A match is at least
-// 3 bytes long, so 4 consecutive flat bytes belong to at most two lanes (the
-// owners of the first and the last byte).  Byte i of lane o's match is read
-// from rpos_o + i, or rpos_o + (i mod dist_o) when the copy overlaps itself
-// (dist_o < ml_o): either way from bytes complete before this pass, so the
-// bytes of a pass may be produced in any order.
-struct MatchLane {
-  uint32_t wpos, rpos, dist, ml, far_lo, far_hi;
-};
-__device__ __forceinline__ void flat_matches(uint8_t* ring, const uint8_t* far_base, const uint8_t* out_blk,
-                                             uint32_t ring_lo, const MatchLane& me, bool go) {
-  const uint32_t lane = lane_id();
-  const uint32_t mc = go ? me.ml : 0u;
-  const uint32_t inc = warp_incl_scan(mc);
-  const uint32_t total = __shfl_sync(FULL, inc, 31);
-  const uint32_t mpre = inc - mc;
-  // per-lane constants: destination and source base relative to the flat index
-  const uint32_t D = me.wpos - mpre, R = me.rpos - mpre, E = mpre + mc, OV = mpre + me.dist;
-  const bool any_overlap = __ballot_sync(FULL, go && me.dist < me.ml) != 0;
-  for (uint32_t k0 = 0; k0 < total; k0 += 128) {
-    const uint32_t k = k0 + 4 * lane;
-    const int o1 = warp_search(mpre, k);
-    const int o2 = warp_search(mpre, k + 3);
-    const uint32_t D1 = __shfl_sync(FULL, D, o1), D2 = __shfl_sync(FULL, D, o2);
-    const uint32_t R1 = __shfl_sync(FULL, R, o1), R2 = __shfl_sync(FULL, R, o2);
-    const uint32_t E1 = __shfl_sync(FULL, E, o1);
-    const uint32_t F01 = __shfl_sync(FULL, me.far_lo, o1), F02 = __shfl_sync(FULL, me.far_lo, o2);
-    const uint32_t F11 = __shfl_sync(FULL, me.far_hi, o1), F12 = __shfl_sync(FULL, me.far_hi, o2);
-    uint32_t OV1 = 0, OV2 = 0, P1 = 0, P2 = 0, d1 = 1, d2 = 1;
-    if (any_overlap) {
-      OV1 = __shfl_sync(FULL, OV, o1);
-      OV2 = __shfl_sync(FULL, OV, o2);
-      P1 = __shfl_sync(FULL, mpre, o1);
-      P2 = __shfl_sync(FULL, mpre, o2);
-      d1 = __shfl_sync(FULL, me.dist, o1);
-      d2 = __shfl_sync(FULL, me.dist, o2);
-    }
-#pragma unroll
-    for (uint32_t b = 0; b < 4; b++) {
-      const uint32_t kk = k + b;
-      if (kk < total) {
-        const bool first = kk < E1;
-        const int o = first ? o1 : o2;
-        const uint32_t Dd = first ? D1 : D2;
-        uint32_t x = (first ? R1 : R2) + kk;
-        if (any_overlap) {
-          const uint32_t ov = first ? OV1 : OV2;
-          if (kk >= ov) {  // overlapping copy: the pattern of the last dist bytes repeats
-            const uint32_t p = first ? P1 : P2, d = first ? d1 : d2;
-            x = (first ? R1 : R2) + p + (kk - p) % d;
-          }
-        }
-        const uint32_t f0 = first ? F01 : F02, f1 = first ? F11 : F12;
-        uint8_t v;
-        if (x >= ring_lo) v = ring[x & RING_MASK];
-        else if (x >= f0 && x < f1) v = far_base[o * FAR_STAGE + (x - f0)];
-        else v = out_blk[x];
-        ring[(Dd + kk) & RING_MASK] = v;
-      }
-    }
-  }
 }
 
 // DE property check of one group (Sec. 4.2): each back-reference's source
@@ -723,9 +593,10 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
           lit_run = 0;
           outp += ml;
         }
+        // a lane that runs past its sub-block stops here (this bounds the
+        // loop on corrupt input); sizes are checked when the sub-block ends
         if (L == 0) err = GMP_STATUS_CORRUPT_SYMBOL;
         else if (pos > end) err = GMP_STATUS_BITSTREAM;
-        else if (outp > out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
         act = !err && q < q_end;
       }
       __syncwarp();
@@ -874,13 +745,16 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       GMP_TSTAMP(tg3);
       GMP_TADD(2, tg2, tg3);
       const SrcView sv{ring, SB.far[stage][lane], out_blk, ring_lo, cur.far_lo, cur.far_hi};
-      if (de && de_group_ok(rpos, wpos, ml)) {
+      // DE: every source below the group start passes at once; otherwise the
+      // exact per-group check decides (de_group_ok)
+      const bool de_ok = de && (__all_sync(FULL, !pending || rpos + ml <= G0) || de_group_ok(rpos, wpos, ml));
+      if (de_ok) {
         if (pending) copy_match_words(ring, sv, rpos, wpos, ml);
         __syncwarp();
         rounds = __ballot_sync(FULL, pending) ? 1 : 0;
       } else {
         if (de) n_fallback++;
-        // Multi-Round Resolution (reading at resolve_mrr): HWM = write
+        // Multi-Round Resolution (reading at resolve_mrr_global): HWM = write
         // position of the lowest pending lane
         bool pend = pending;
         rounds = 0;
@@ -924,14 +798,13 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       __syncwarp();
       for (uint32_t i = 0; i < ll; i++) out_blk[dst + i] = shadow[lsrc + i];
       __syncwarp();
-      SrcMap m{ring, SB.far[stage][lane], out_blk, 0, 0, 0};
       if (de && de_group_ok(rpos, wpos, ml)) {
         if (pending) copy_match_global(out_blk, rpos, wpos, ml);
         __syncwarp();
         rounds = __ballot_sync(FULL, pending) ? 1 : 0;
       } else {
         if (de) n_fallback++;
-        rounds = resolve_mrr<false>(ring, m, out_blk, rpos, wpos, ml, pending);
+        rounds = resolve_mrr_global(out_blk, rpos, wpos, ml, pending);
       }
       flushed = G1;
       ring_valid_lo = G1;
