@@ -358,6 +358,94 @@ def run_gmp(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched workload: many independent files of uneven sizes (log-uniform
+    4 KiB..16 MiB, seeded text/CSV and MRR/DE coins) decoded in ONE
+    persistent launch replayed from a CUDA graph, against one gmp_decompress
+    launch per file on the same stream.  Block size and sub-blocks per block
+    come from the format autotuner on a sample of the mix."""
+    import torch
+    import paper_1606_00519_gb300 as gmp
+    from paper_1606_00519_gb300 import autotune
+
+    torch.cuda.set_device(0)
+    cap = None if args.batch_cap == 0 else args.batch_cap
+    mix = datagen.file_mix(seed=4, n_files=args.batch_files, lo=4 * KiB, hi=16 * MiB, total_cap=cap)
+    # a sample large enough to fill the GPU (the tuner times throughput, not
+    # the latency of a small input): the first files of the mix, 128 MiB
+    parts, got = [], 0
+    for sz, kind, mode, sd in mix:
+        if got >= 128 * MiB:
+            break
+        parts.append(datagen.make_data(kind, sz, sd))
+        got += sz
+    sample = np.concatenate(parts)
+    t0 = time.perf_counter()
+    tuned = autotune.tune(sample, block_sizes=(128 * KiB, 256 * KiB), n_subs=(32, 64), repeats=3)
+    t_tune = time.perf_counter() - t0
+    bs, k = tuned["block_size"], tuned["n_sub"]
+    files, total, comp_total = [], 0, 0
+    for size, kind, mode, sd in mix:
+        data = datagen.make_data(kind, size, sd)
+        st = gmp.compress(data, bs, k, 32 * KiB, de=(mode == "de"))
+        ds = gmp.DeviceStream(st)
+        ref = torch.from_numpy(data).cuda()
+        out = torch.empty(max(size, 16), dtype=torch.uint8, device="cuda")
+        files.append((ds, out, ref))
+        total += size
+        comp_total += st.size
+    table = gmp.make_file_table([ds.file_desc(out, ds.orig_size) for ds, out, _ in files])
+    status = torch.zeros(len(files), dtype=torch.int32, device="cuda")
+    ctx = gmp.Context(max_block_out=bs, max_files=len(files))
+    ctx.set_launch(tuned["warps_per_cta"], tuned["ctas_per_sm"])
+    graph = ctx.batch_graph(table, len(files), status)
+    stream = torch.cuda.current_stream()
+
+    def check():
+        torch.cuda.synchronize()
+        assert int(status.abs().sum().item()) == 0, "batch: a file reported an error"
+        for ds, out, ref in files:
+            if not torch.equal(out[:ds.orig_size], ref):
+                raise SystemExit("batch: output differs from the input")
+
+    graph.launch(stream)
+    check()
+    for _ in range(args.warmup):
+        graph.launch(stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        graph.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = a.elapsed_time(b) / args.steps
+    # one launch per file
+    st1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for ds, out, _ in files:
+        ctx.decompress_into(ds, out, st1, stream)
+    check()
+    a.record(stream)
+    for _ in range(args.steps):
+        for ds, out, _ in files:
+            ctx.decompress_into(ds, out, st1, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    per_file_ms = a.elapsed_time(b) / args.steps
+    check()
+    line = {"metric": "batched decompressed GB/s", "value": round(total / (graph_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(graph_ms, 4),
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"batch: {len(files)} files, log-uniform 4 KiB..16 MiB, text/CSV and MRR/DE mixed"
+                                   + (f", seeded prefix up to {cap} bytes" if cap else ""),
+                       "total_bytes": total, "compressed_bytes": comp_total, "ratio": round(total / comp_total, 4),
+                       "tuned": tuned, "tune_seconds": round(t_tune, 2)},
+            "one_launch_per_file": {"value": round(total / (per_file_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+                                    "ms_per_step": round(per_file_ms, 4)},
+            "speedup_vs_one_launch_per_file": round(per_file_ms / graph_ms, 3)}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving: Poisson arrivals of requests (16 KiB..64 MiB, mixed content
     and modes) admitted under a device-memory budget by the continuous-batching
@@ -466,6 +554,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
     ap.add_argument("--ref-blocks", type=int, default=16, help="oracle blocks per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="batched many-file benchmark instead of the decode step")
+    ap.add_argument("--batch-files", type=int, default=4096)
+    ap.add_argument("--batch-cap", type=int, default=GiB, help="seeded prefix of the file list up to this many bytes "
+                                                                 "(0: all files)")
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the decode step")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-pool", type=int, default=96)
@@ -474,7 +566,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.serve:
+    if args.batch:
+        run_batch(args)
+    elif args.serve:
         run_serve(args)
     elif args.impl == "reference":
         run_reference(args)

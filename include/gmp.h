@@ -224,6 +224,21 @@ int gmp_graph_launch(gmp_graph* g, void* stream);
 void gmp_graph_destroy(gmp_graph* g);
 
 /* ------------------------------------------------------------------------ */
+/* Launch-shape autotuner: times the batched decode of a sample (device file
+   descriptors, as for gmp_decompress_batch) under several shapes (warps per
+   CTA 1, 2, 4, 8, 16; CTAs per SM as many as fit and half of that), keeps
+   the fastest in the context and reports it.  Each shape is run once to
+   warm up and three times timed with CUDA events on `stream`; the context's
+   scratch is reallocated when a shape needs more.  Synchronous. */
+typedef struct {
+  uint32_t warps_per_cta, ctas_per_sm; /* the chosen shape */
+  double best_ms;                      /* its mean time per batched launch */
+  uint32_t shapes_tried;
+} gmp_tuning;
+int gmp_autotune(gmp_context* ctx, const gmp_file_desc* d_files, size_t n_files, int32_t* d_status, void* stream,
+                 gmp_tuning* out);
+
+/* ------------------------------------------------------------------------ */
 /* Statistics of the launches since gmp_stats_reset (collect_stats=1):
    32-sequence groups resolved, MRR rounds, groups of a DE stream that broke
    the DE property and were resolved by MRR, blocks decoded, the largest

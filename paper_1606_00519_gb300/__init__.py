@@ -21,7 +21,8 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _native
-from ._native import BlockRef, Completion, CompressOpts, ContextOpts, FileDesc, ServerOpts, Stats, StreamInfo
+from ._native import (BlockRef, Completion, CompressOpts, ContextOpts, FileDesc, ServerOpts, Stats, StreamInfo,
+                      Tuning)
 
 OK = 0
 STATUS_NAMES = {0: "OK", 1: "BAD_HEADER", 2: "CORRUPT_SYMBOL", 3: "BITSTREAM", 4: "BAD_OFFSET",
@@ -201,6 +202,16 @@ class Context:
                                               ctypes.c_void_p(status.data_ptr()), None, ctypes.byref(g)),
                "gmp_batch_graph_create")
         return Graph(self._L, g)
+
+    def autotune(self, files_dev, n_files: int, status, stream=None) -> dict:
+        """Time the batched decode of a sample under several launch shapes
+        (gmp_autotune) and keep the fastest; returns the chosen shape."""
+        t = Tuning()
+        _check(self._L.gmp_autotune(self._h, ctypes.c_void_p(files_dev.data_ptr()), n_files,
+                                    ctypes.c_void_p(status.data_ptr()), _stream_handle(stream), ctypes.byref(t)),
+               "gmp_autotune")
+        return {"warps_per_cta": t.warps_per_cta, "ctas_per_sm": t.ctas_per_sm, "best_ms": t.best_ms,
+                "shapes_tried": t.shapes_tried}
 
     def stats_reset(self, stream=None):
         _check(self._L.gmp_stats_reset(self._h, _stream_handle(stream)), "gmp_stats_reset")

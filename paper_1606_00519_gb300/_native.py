@@ -118,6 +118,11 @@ class Completion(ctypes.Structure):
                 ("t_done", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("best_ms", ctypes.c_double),
+                ("shapes_tried", ctypes.c_uint32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("de_fallback_groups", ctypes.c_uint64),
                 ("blocks", ctypes.c_uint64), ("max_rounds", ctypes.c_uint64),
@@ -149,6 +154,7 @@ def _declare(L):
     L.gmp_graph_launch.argtypes = [vp, vp]
     L.gmp_graph_destroy.argtypes = [vp]
     L.gmp_graph_destroy.restype = None
+    L.gmp_autotune.argtypes = [vp, vp, sz, vp, vp, P(Tuning)]
     L.gmp_stats_reset.argtypes = [vp, vp]
     L.gmp_stats_read.argtypes = [vp, P(Stats)]
     L.gmp_decompress_host.argtypes = [vp, vp, sz, vp, sz, P(ctypes.c_int32), vp]

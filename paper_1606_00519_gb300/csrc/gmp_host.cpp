@@ -324,6 +324,66 @@ void gmp_graph_destroy(gmp_graph* g) {
   delete g;
 }
 
+int gmp_autotune(gmp_context* c, const gmp_file_desc* d_files, size_t n_files, int32_t* d_status, void* stream,
+                 gmp_tuning* out) {
+  if (!c || !out || !d_files || !d_status || n_files == 0) return GMP_ERR_INVALID_ARG;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  GMP_CUDA(cudaEventCreate(&e0));
+  GMP_CUDA(cudaEventCreate(&e1));
+  const gmp_context_opts saved = c->opts;
+  double best = 1e300;
+  uint32_t best_w = 0, best_c = 0, tried = 0;
+  int rc = GMP_OK;
+  for (uint32_t w : {1u, 2u, 4u, 8u, 16u}) {
+    int occ = 0;
+    const size_t smem = (size_t)w * gmp::warp_smem_bytes();
+    if (gmp::configure_kernel(smem) != cudaSuccess || gmp::occupancy((int)w, smem, &occ) != cudaSuccess || occ < 1)
+      continue;
+    for (int cps : {occ, occ / 2}) {
+      if (cps < 1 || (cps == occ / 2 && occ / 2 == occ)) continue;
+      c->opts.warps_per_cta = w;
+      c->opts.ctas_per_sm = (uint32_t)cps;
+      if ((rc = context_alloc_scratch(c)) != GMP_OK) break;
+      if ((rc = gmp_decompress_batch(c, d_files, n_files, d_status, s)) != GMP_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3 && rc == GMP_OK; r++) rc = gmp_decompress_batch(c, d_files, n_files, d_status, s);
+      cudaEventRecord(e1, s);
+      if (rc) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "gmp_autotune");
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tried++;
+      if (ms / 3.0 < best) {
+        best = ms / 3.0;
+        best_w = w;
+        best_c = (uint32_t)cps;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == GMP_OK && tried) {
+    c->opts.warps_per_cta = best_w;
+    c->opts.ctas_per_sm = best_c;
+    rc = context_alloc_scratch(c);
+    out->warps_per_cta = best_w;
+    out->ctas_per_sm = best_c;
+    out->best_ms = best;
+    out->shapes_tried = tried;
+  } else {
+    c->opts = saved;
+    int rc2 = context_alloc_scratch(c);
+    if (rc == GMP_OK) rc = tried ? rc2 : GMP_ERR_CUDA;
+  }
+  return rc;
+}
+
 int gmp_stats_reset(gmp_context* c, void* stream) {
   if (!c) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
