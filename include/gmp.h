@@ -145,6 +145,7 @@ typedef struct {
   uint32_t chain_depth; /* match candidates tried per position (default 64) */
   uint32_t de;          /* 1: Dependency Elimination (Sec. 4.2), 0: plain (MRR) */
   uint32_t n_threads;   /* host threads, 0 = all cores */
+  uint32_t lazy;        /* 1: one-step lazy match evaluation (default), 0: greedy */
 } gmp_compress_opts;
 
 void gmp_compress_opts_default(gmp_compress_opts* o);

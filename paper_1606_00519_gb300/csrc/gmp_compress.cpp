@@ -52,60 +52,79 @@ inline uint32_t hash_at(const uint8_t* p) {
   return (x * 0x9E3779B1u) >> (32 - kHashBits);
 }
 
-// Greedy LZ77 over one block.
+// LZ77 over one block: at each position the longest match among the hash
+// chain's candidates (nearest first on ties); with o.lazy, while the next
+// position has a longer match, the current byte becomes a literal and the
+// search moves on (one-step lazy evaluation).  Fewer, longer sequences make
+// the stream smaller and faster to decode.
 void parse_block(const uint8_t* in, uint32_t n, const gmp_compress_opts& o, std::vector<Seq>& seqs,
                  std::vector<uint32_t>& head, std::vector<uint32_t>& chain) {
   seqs.clear();
   std::fill(head.begin(), head.end(), kNil);
   if (chain.size() < n) chain.resize(n);
-  uint32_t lit_start = 0, i = 0;
+  uint32_t lit_start = 0, i = 0, ins = 0;
   // DE: output intervals of the back-references of the current group
   uint32_t grp_lo[32], grp_hi[32];
   uint32_t in_grp = 0;
-  auto insert = [&](uint32_t p) {
-    if (p + 3 <= n) {
-      uint32_t h = hash_at(in + p);
-      chain[p] = head[h];
-      head[h] = p;
+  auto insert_upto = [&](uint32_t p) {  // every position below p is in the chains
+    for (; ins < p; ins++) {
+      if (ins + 3 <= n) {
+        const uint32_t h = hash_at(in + ins);
+        chain[ins] = head[h];
+        head[h] = ins;
+      }
+    }
+  };
+  auto find = [&](uint32_t p, uint32_t& best_len, uint32_t& best_dist) {
+    best_len = best_dist = 0;
+    if (p + 3 > n) return;
+    const uint32_t lim = std::min<uint32_t>(o.max_match, n - p);
+    uint32_t cand = head[hash_at(in + p)];
+    for (uint32_t tries = 0; cand != kNil && tries < o.chain_depth; tries++, cand = chain[cand]) {
+      const uint32_t dist = p - cand;
+      if (dist > o.window) break;
+      if (best_len < lim && in[cand + best_len] != in[p + best_len]) continue;  // cannot beat best
+      uint32_t len = 0;
+      while (len < lim && in[cand + len] == in[p + len]) len++;
+      if (o.de) {
+        // the source bytes before p must avoid this group's earlier copies
+        const uint32_t src_end = std::min(cand + len, p);
+        for (uint32_t g = 0; g < in_grp; g++) {
+          if (grp_hi[g] > cand && grp_lo[g] < src_end) len = std::min(len, grp_lo[g] > cand ? grp_lo[g] - cand : 0u);
+        }
+      }
+      if (len >= 3 && len > best_len) {
+        best_len = len;
+        best_dist = dist;
+        if (len == lim) break;
+      }
     }
   };
   while (i < n) {
-    uint32_t best_len = 0, best_dist = 0;
-    if (i + 3 <= n) {
-      const uint32_t lim = std::min<uint32_t>(o.max_match, n - i);
-      uint32_t cand = head[hash_at(in + i)];
-      for (uint32_t tries = 0; cand != kNil && tries < o.chain_depth; tries++, cand = chain[cand]) {
-        const uint32_t dist = i - cand;
-        if (dist > o.window) break;
-        if (in[cand + best_len] != in[i + best_len] && best_len < lim) continue;  // cannot beat best
-        uint32_t len = 0;
-        while (len < lim && in[cand + len] == in[i + len]) len++;
-        if (o.de) {
-          // the source bytes before i must avoid this group's earlier copies
-          const uint32_t src_end = std::min(cand + len, i);
-          for (uint32_t g = 0; g < in_grp; g++) {
-            if (grp_hi[g] > cand && grp_lo[g] < src_end) len = std::min(len, grp_lo[g] > cand ? grp_lo[g] - cand : 0u);
-          }
-        }
-        if (len >= 3 && len > best_len) {
-          best_len = len;
-          best_dist = dist;
-          if (len == lim) break;
-        }
+    insert_upto(i);
+    uint32_t len = 0, dist = 0;
+    find(i, len, dist);
+    if (len && o.lazy) {
+      while (i + 1 < n && len < o.max_match) {
+        insert_upto(i + 1);
+        uint32_t l2 = 0, d2 = 0;
+        find(i + 1, l2, d2);
+        if (l2 <= len) break;
+        i++;  // the byte at i stays a literal
+        len = l2;
+        dist = d2;
       }
     }
-    if (best_len) {
-      seqs.push_back(Seq{lit_start, i - lit_start, best_len, best_dist});
-      for (uint32_t k = 0; k < best_len; k++) insert(i + k);
+    if (len) {
+      seqs.push_back(Seq{lit_start, i - lit_start, len, dist});
       if (o.de) {
         grp_lo[in_grp] = i;
-        grp_hi[in_grp] = i + best_len;
+        grp_hi[in_grp] = i + len;
         if (++in_grp == 32) in_grp = 0;
       }
-      i += best_len;
+      i += len;
       lit_start = i;
     } else {
-      insert(i);
       i++;
     }
   }
@@ -318,6 +337,7 @@ void gmp_compress_opts_default(gmp_compress_opts* o) {
   o->chain_depth = 64;
   o->de = 0;
   o->n_threads = 0;
+  o->lazy = 1;
 }
 
 size_t gmp_compress_bound(size_t n, const gmp_compress_opts* o) {

@@ -316,11 +316,19 @@ __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v
   uint32_t i = 0;
   const bool in_ring = rpos >= v.ring_lo;                                      // whole source in the ring
   const bool in_far = !in_ring && rpos >= v.far_lo && rpos + ml <= v.far_hi;   // whole source staged
-  if (wpos - rpos < 4 || !(in_ring || in_far)) {
+  if (!(in_ring || in_far)) {
     for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
     return;
   }
-  for (; i < ml && ((wpos + i) & 3u); i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+  // one linear view of the source: byte x at base[(x - off) & mask]
+  const uint8_t* base = in_ring ? v.ring : v.far;
+  const uint32_t off = in_ring ? 0u : v.far_lo;
+  const uint32_t mask = in_ring ? RING_MASK : 0xffffffffu;
+  if (wpos - rpos < 4) {  // distance 1..3 (a ring source): the pattern repeats byte by byte
+    for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
+    return;
+  }
+  for (; i < ml && ((wpos + i) & 3u); i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
   uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
   if (in_ring) {
     for (; i + 4 <= ml; i += 4) {
@@ -337,7 +345,7 @@ __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v
       r32[((wpos + i) >> 2) & RING_WMASK] = __funnelshift_r(f32[r >> 2], f32[(r >> 2) + 1], (r & 3u) * 8u);
     }
   }
-  for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+  for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
 }
 
 // DE property check of one group (Sec. 4.2): each back-reference's source
