@@ -330,16 +330,39 @@ __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v
   }
   for (; i < ml && ((wpos + i) & 3u); i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
   uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
+  // with a distance of 16 or more, the 16 source bytes of a step lie before
+  // the step's destination, so its five loads issue together (one shared
+  // memory latency per 16 bytes instead of per 4)
+  const bool wide = wpos - rpos >= 16;
   if (in_ring) {
+    if (wide) {
+      for (; i + 16 <= ml; i += 16) {
+        const uint32_t x = rpos + i, wa = x >> 2, sh = (x & 3u) * 8u, d = (wpos + i) >> 2;
+        const uint32_t w0 = r32[wa & RING_WMASK], w1 = r32[(wa + 1) & RING_WMASK], w2 = r32[(wa + 2) & RING_WMASK];
+        const uint32_t w3 = r32[(wa + 3) & RING_WMASK], w4 = r32[(wa + 4) & RING_WMASK];
+        r32[d & RING_WMASK] = __funnelshift_r(w0, w1, sh);
+        r32[(d + 1) & RING_WMASK] = __funnelshift_r(w1, w2, sh);
+        r32[(d + 2) & RING_WMASK] = __funnelshift_r(w2, w3, sh);
+        r32[(d + 3) & RING_WMASK] = __funnelshift_r(w3, w4, sh);
+      }
+    }
     for (; i + 4 <= ml; i += 4) {
       const uint32_t x = rpos + i, wa = x >> 2;
       r32[((wpos + i) >> 2) & RING_WMASK] =
           __funnelshift_r(r32[wa & RING_WMASK], r32[(wa + 1) & RING_WMASK], (x & 3u) * 8u);
     }
   } else {
-    // staged source: a plain array (the pair read may run up to one word
-    // past the lane's slot, into other staging; those bytes are discarded)
+    // staged source: a plain array (the reads may run up to one word past
+    // the lane's slot, into other staging; those bytes are discarded)
     const uint32_t* f32 = reinterpret_cast<const uint32_t*>(v.far);
+    for (; i + 16 <= ml; i += 16) {
+      const uint32_t r = rpos - v.far_lo + i, wa = r >> 2, sh = (r & 3u) * 8u, d = (wpos + i) >> 2;
+      const uint32_t w0 = f32[wa], w1 = f32[wa + 1], w2 = f32[wa + 2], w3 = f32[wa + 3], w4 = f32[wa + 4];
+      r32[d & RING_WMASK] = __funnelshift_r(w0, w1, sh);
+      r32[(d + 1) & RING_WMASK] = __funnelshift_r(w1, w2, sh);
+      r32[(d + 2) & RING_WMASK] = __funnelshift_r(w2, w3, sh);
+      r32[(d + 3) & RING_WMASK] = __funnelshift_r(w3, w4, sh);
+    }
     for (; i + 4 <= ml; i += 4) {
       const uint32_t r = rpos - v.far_lo + i;
       r32[((wpos + i) >> 2) & RING_WMASK] = __funnelshift_r(f32[r >> 2], f32[(r >> 2) + 1], (r & 3u) * 8u);
@@ -659,25 +682,30 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     q.ml = r.y & 0xffu;
     const uint32_t dist = r.y >> 8;
     const uint32_t tot = q.ll + q.ml;
-    // one scan of (literal length << 16 | total length) when the group fits
-    // in 16 bits (every group the ring takes), else two scans
-    const uint32_t gsum = __reduce_add_sync(FULL, tot);
+    // one reduction and one scan of (literal length << 16 | total length)
+    // when no lane has 2048 bytes or more (so both halves stay below 2^16),
+    // else two of each
     uint32_t inc_tot, inc_ll;
-    if (gsum < 65536u) {
-      const uint32_t inc = warp_incl_scan((q.ll << 16) | tot);
+    if (!__any_sync(FULL, tot >= 2048u)) {
+      const uint32_t packed = (q.ll << 16) | tot;
+      const uint32_t sum = __reduce_add_sync(FULL, packed);
+      const uint32_t inc = warp_incl_scan(packed);
+      q.gtot = sum & 0xffffu;
+      q.glits = sum >> 16;
       inc_tot = inc & 0xffffu;
       inc_ll = inc >> 16;
     } else {
+      q.gtot = __reduce_add_sync(FULL, tot);
+      q.glits = __reduce_add_sync(FULL, q.ll);
       inc_tot = warp_incl_scan(tot);
       inc_ll = warp_incl_scan(q.ll);
     }
-    q.gtot = gsum;
-    q.glits = __reduce_add_sync(FULL, q.ll);
     q.lpre = inc_ll - q.ll;
     q.dst = G0h + inc_tot - tot;
+    // sub-block of the lane's sequence (lanes past the block's end run to
+    // the last sub-block, so lane 31's cursor bounds every valid lane's)
     uint32_t j = jc;
-    if (q.valid)
-      while (j + 1 < K && t >= S.sb_seq[j + 1]) j++;
+    while (j + 1 < K && t >= S.sb_seq[j + 1]) j++;
     q.lsrc = S.sb_lit[j] + litposh + inc_ll - q.ll;
     q.jnext = __shfl_sync(FULL, j, 31);
     q.wpos = q.dst + q.ll;
@@ -693,7 +721,9 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         const uint32_t a0 = q.rpos & ~15u;
         const uint32_t a1 = min((fe + 15u) & ~15u, flushed & ~15u);
         uint8_t* dstage = SB.far[stage][lane];
-        for (uint32_t c = a0; c < a1; c += 16u) cp_async16(dstage + (c - a0), out_blk + c);
+#pragma unroll
+        for (uint32_t c = 0; c < (uint32_t)FAR_STAGE / 16u; c++)
+          if (a0 + 16u * c < a1) cp_async16(dstage + 16u * c, out_blk + a0 + 16u * c);
         q.far_lo = a0;
         q.far_hi = a1 > a0 ? a1 : a0;
       }
@@ -701,11 +731,9 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     // the group's literals, one contiguous run of the shadow when they all
     // belong to one sub-block: lane i stages the run's i-th 16-byte chunk
     if (allow && q.glits > 0 && q.gtot <= GROUP_FAST_MAX) {
-      const uint32_t last = 31u - (uint32_t)__clz(__ballot_sync(FULL, q.valid) | 1u);
-      const uint32_t j_first = __shfl_sync(FULL, j, 0), j_last = __shfl_sync(FULL, j, last);
-      const uint32_t base = __shfl_sync(FULL, q.lsrc, 0);
+      const uint32_t base = S.sb_lit[jc] + litposh;  // lane 0's literal source
       const uint32_t l0 = base & ~15u, l1 = (base + q.glits + 15u) & ~15u;
-      if (j_first == j_last && l1 - l0 <= (uint32_t)LIT_STAGE) {
+      if (jc == q.jnext && l1 - l0 <= (uint32_t)LIT_STAGE) {
         const uint32_t c = l0 + 16u * lane;
         if (c < l1) cp_async16(SB.lit[stage] + (c - l0), shadow + c);
         q.lit_lo = l0;
