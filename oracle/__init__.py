@@ -57,7 +57,7 @@ def build(force: bool = False) -> str:
 class Params(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("n_sub", ctypes.c_uint32), ("window", ctypes.c_uint32),
                 ("cwl", ctypes.c_uint32), ("min_match", ctypes.c_uint32), ("max_match", ctypes.c_uint32),
-                ("chain_depth", ctypes.c_uint32), ("de", ctypes.c_uint32)]
+                ("chain_depth", ctypes.c_uint32), ("de", ctypes.c_uint32), ("byte_mode", ctypes.c_uint32)]
 
 
 class Info(ctypes.Structure):
@@ -137,8 +137,11 @@ def _bytes(x) -> np.ndarray:
 
 
 def params(block_size=64 * 1024, n_sub=16, window=8 * 1024, cwl=12, max_match=64, chain_depth=64,
-           de=False) -> Params:
-    return Params(block_size, n_sub, window, cwl, 3, max_match, chain_depth, 1 if de else 0)
+           de=False, byte_mode=False) -> Params:
+    """Compressor parameters; byte_mode selects Gompresso/Byte records
+    (no Huffman trees, n_sub and cwl unused)."""
+    return Params(block_size, n_sub, window, cwl, 3, max_match, chain_depth, 1 if de else 0,
+                  1 if byte_mode else 0)
 
 
 # ---------------------------------------------------------------- primitives

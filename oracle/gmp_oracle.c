@@ -53,6 +53,14 @@
  *   offset symbols: distance d, v = d - 1: v < 4 -> symbol v; else with
  *   k = floor(log2 v): symbol 2k + bit (k-1) of v, then k-1 extra bits
  *   v mod 2^(k-1), written LSB-first after the symbol.
+ *   Byte streams (Gompresso/Byte, Sec. 3.1 and 3.2: byte-level encoding, no
+ *   Huffman trees; flags bit1 = 0, n_sub = cwl = 0): block = u32 n_seq, u32
+ *   out_bytes, u32 n_lit, u32 0, then n_seq 4-byte records (bits 0-9 literal
+ *   length 0..1023, bits 10-15 match code m: 0 = no back-reference, 1..62 =
+ *   length m + 2, bits 16-31 distance - 1), zero padding to 16 bytes, the
+ *   n_lit literal bytes of the block in order, zero padding to 16 bytes.  A
+ *   literal string longer than 1023 bytes is cut into literal-only
+ *   sequences, which the parse counts like any other sequence.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -90,6 +98,7 @@ typedef struct {
   uint32_t max_match;
   uint32_t chain_depth;
   uint32_t de;
+  uint32_t byte_mode; /* 1: Gompresso/Byte records instead of Huffman bitstreams */
 } orc_params;
 
 static void put16(uint8_t* p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
@@ -359,6 +368,14 @@ static int lz77_block(const uint8_t* in, uint32_t n, const orc_params* P, seqbuf
     } else {
       INSERT(pos);
       pos++;
+      if (P->byte_mode && pos - lit_start == 1023 && pos < n) {
+        /* a Byte record holds at most 1023 literals: close a literal-only
+           sequence (it counts towards the DE group like any other) */
+        rc = seq_push(out, in + lit_start, 1023, 0, 0);
+        if (rc) break;
+        lit_start = pos;
+        if (++in_group == 32) in_group = 0;
+      }
     }
   }
   if (!rc && lit_start < n) rc = seq_push(out, in + lit_start, n - lit_start, 0, 0);
@@ -453,7 +470,32 @@ static int64_t encode_block(const seqbuf* S, uint32_t out_bytes, const orc_param
   return (int64_t)(bs_off + up16((w.nbits + 7) / 8));
 }
 
+/* Byte-level block (Gompresso/Byte): fixed 4-byte records, then the
+   literal bytes.  Returns the bytes written or a negative error. */
+static int64_t encode_block_byte(const seqbuf* S, uint32_t out_bytes, const orc_params* P, uint8_t* dst,
+                                 uint64_t cap) {
+  uint64_t rec_end = up16(16 + 4ull * S->n);
+  uint64_t total = rec_end + up16(S->nlits);
+  if (total > cap) return ORC_ERR_CAP;
+  memset(dst, 0, total);
+  put32(dst, (uint32_t)S->n);
+  put32(dst + 4, out_bytes);
+  put32(dst + 8, (uint32_t)S->nlits);
+  for (size_t i = 0; i < S->n; i++) {
+    uint32_t ll = S->lit_len[i], ml = S->mlen[i], d = S->off[i];
+    if (ll > 1023) return ORC_ERR_ARG;
+    if (ml && (ml < P->min_match || ml > P->max_match || d < 1 || d > 65536)) return ORC_ERR_ARG;
+    uint32_t rec = ll | ((ml ? ml - 2 : 0u) << 10) | ((ml ? d - 1 : 0u) << 16);
+    put32(dst + 16 + 4 * i, rec);
+  }
+  memcpy(dst + rec_end, S->lits, S->nlits);
+  return (int64_t)total;
+}
+
 static int params_ok(const orc_params* P) {
+  if (P->byte_mode)
+    return P->block_size >= 1 && P->window >= 1 && P->window <= 32768 && P->min_match == 3 &&
+           P->max_match >= 3 && P->max_match <= 64 && P->chain_depth >= 1;
   return P->block_size >= 1 && P->n_sub >= 1 && P->n_sub <= 64 && P->window >= 1 && P->window <= 32768 &&
          P->cwl >= 1 && P->cwl <= MAX_CWL && P->min_match == 3 && P->max_match >= 3 && P->max_match <= 64 &&
          P->chain_depth >= 1;
@@ -462,6 +504,8 @@ static int params_ok(const orc_params* P) {
 uint64_t orc_compress_bound(uint64_t n, const orc_params* P) {
   uint64_t nb = (n + P->block_size - 1) / P->block_size;
   /* every byte a literal of at most 12 bits plus one end symbol per block */
+  /* Byte streams: at most one 4-byte record per byte plus the literals */
+  if (P->byte_mode) return HDR_BYTES + up16(8 * nb) + nb * 48 + 5 * n + 64;
   return HDR_BYTES + up16(8 * nb) + nb * (up16(BLK_FIXED + 12ull * P->n_sub) + 32) + (n * 12 + 7) / 8 +
          nb * 2 + 64;
 }
@@ -470,10 +514,10 @@ static void write_header(uint8_t* out, const orc_params* P, uint64_t n, uint64_t
   memset(out, 0, HDR_BYTES);
   memcpy(out, "GMP1", 4);
   put16(out + 4, 1);
-  put16(out + 6, (P->de ? 1u : 0u) | 2u);
+  put16(out + 6, (P->de ? 1u : 0u) | (P->byte_mode ? 0u : 2u));
   put32(out + 8, P->block_size);
-  put16(out + 12, P->n_sub);
-  out[14] = (uint8_t)P->cwl;
+  put16(out + 12, P->byte_mode ? 0u : P->n_sub);
+  out[14] = (uint8_t)(P->byte_mode ? 0u : P->cwl);
   put32(out + 16, P->window);
   out[20] = (uint8_t)P->min_match;
   out[21] = (uint8_t)P->max_match;
@@ -497,7 +541,8 @@ int64_t orc_compress(const uint8_t* in, uint64_t n, const orc_params* P, uint8_t
     int rc = lz77_block(in + s, len, P, &S);
     if (rc) { seq_free(&S); return rc; }
     put64(out + HDR_BYTES + 8 * b, pos);
-    int64_t w = encode_block(&S, len, P, out + pos, cap - pos);
+    int64_t w = P->byte_mode ? encode_block_byte(&S, len, P, out + pos, cap - pos)
+                             : encode_block(&S, len, P, out + pos, cap - pos);
     seq_free(&S);
     if (w < 0) return w;
     pos += (uint64_t)w;
@@ -537,7 +582,8 @@ int64_t orc_encode_tokens(const uint32_t* lit_len, const uint32_t* mlen, const u
   if (cap < pos + 16) return ORC_ERR_CAP;
   memset(out, 0, pos);
   put64(out + HDR_BYTES, pos);
-  int64_t w = encode_block(&S, (uint32_t)tot, P, out + pos, cap - pos);
+  int64_t w = P->byte_mode ? encode_block_byte(&S, (uint32_t)tot, P, out + pos, cap - pos)
+                           : encode_block(&S, (uint32_t)tot, P, out + pos, cap - pos);
   if (w < 0) return w;
   pos += (uint64_t)w;
   if (cap < pos + 16) return ORC_ERR_CAP;
@@ -566,7 +612,12 @@ int orc_stream_info(const uint8_t* s, uint64_t len, orc_info* I) {
   I->orig_size = get64(s + 24);
   I->n_blocks = get64(s + 32);
   I->stream_bytes = get64(s + 40);
-  if (!(I->flags & 2u) || I->block_size == 0 || I->n_sub == 0 || I->n_sub > 64 || I->cwl == 0 ||
+  if (!(I->flags & 2u)) {
+    /* Byte stream: no trees, no sub-blocks */
+    if (I->n_sub != 0 || I->cwl != 0 || I->block_size == 0 || I->window == 0 || I->window > 32768 ||
+        I->min_match != 3 || I->max_match < 3 || I->max_match > 64)
+      return ORC_BAD_HEADER;
+  } else if (I->block_size == 0 || I->n_sub == 0 || I->n_sub > 64 || I->cwl == 0 ||
       I->cwl > MAX_CWL || I->window == 0 || I->window > 32768 || I->min_match != 3 || I->max_match < 3 ||
       I->max_match > 64)
     return ORC_BAD_HEADER;
@@ -626,8 +677,39 @@ static int canon_decode(const canon* c, int cwl, bitr* r) {
 
 /* Decode the sequences of block b, checking every sub-block against its
    stored bit size, output size and sequence count.  Caller frees S.        */
+/* Sequences of a Byte block: the records in order, literals from the
+   block's literal section (format in the header comment). */
+static int block_tokens_byte(const uint8_t* s, uint64_t len, const orc_info* I, uint64_t b, seqbuf* S,
+                             uint32_t* out_bytes_p) {
+  uint64_t bo = get64(s + HDR_BYTES + 8 * b);
+  if (bo & 15 || bo + 16 > len) return ORC_BAD_HEADER;
+  const uint8_t* B = s + bo;
+  uint32_t n_seq = get32(B), out_bytes = get32(B + 4), n_lit = get32(B + 8);
+  uint64_t expect = b + 1 < I->n_blocks ? I->block_size : I->orig_size - b * (uint64_t)I->block_size;
+  if (out_bytes != expect) return ORC_BAD_HEADER;
+  uint64_t lit_off = up16(16 + 4ull * n_seq);
+  if (bo + lit_off + n_lit > len) return ORC_BAD_HEADER;
+  uint64_t lp = 0, produced = 0;
+  for (uint32_t i = 0; i < n_seq; i++) {
+    uint32_t rec = get32(B + 16 + 4ull * i);
+    uint32_t ll = rec & 1023u, m = (rec >> 10) & 63u;
+    if (m > 62) return ORC_CORRUPT_SYMBOL;
+    uint32_t ml = m ? m + 2 : 0, d = m ? (rec >> 16) + 1 : 0;
+    if (ml > I->max_match) return ORC_CORRUPT_SYMBOL;
+    if (lp + ll > n_lit) return ORC_OUTPUT_OVERRUN;
+    if (seq_push(S, B + lit_off + lp, ll, ml, d)) return ORC_ERR_NOMEM;
+    lp += ll;
+    produced += ll + ml;
+    if (produced > out_bytes) return ORC_OUTPUT_OVERRUN;
+  }
+  if (lp != n_lit || produced != out_bytes) return ORC_OUTPUT_OVERRUN;
+  *out_bytes_p = out_bytes;
+  return 0;
+}
+
 static int block_tokens(const uint8_t* s, uint64_t len, const orc_info* I, uint64_t b, seqbuf* S,
                         uint32_t* out_bytes_p) {
+  if (!(I->flags & 2u)) return block_tokens_byte(s, len, I, b, S, out_bytes_p);
   uint64_t bo = get64(s + HDR_BYTES + 8 * b);
   uint64_t bs_off = up16(BLK_FIXED + 12ull * I->n_sub);
   if (bo & 15 || bo + bs_off > len) return ORC_BAD_HEADER;
@@ -907,15 +989,22 @@ int orc_validate(const uint8_t* s, uint64_t len, orc_report* R) {
   memset(&st, 0, sizeof(st));
   for (uint64_t b = 0; b < I.n_blocks; b++) {
     uint64_t bo = get64(s + HDR_BYTES + 8 * b);
-    if (bo + BLK_FIXED > len) { R->blocks_ok = 0; R->first_error = ORC_BAD_HEADER; return ORC_BAD_HEADER; }
+    if (bo + ((I.flags & 2u) ? BLK_FIXED : 16u) > len) {
+      R->blocks_ok = 0;
+      R->first_error = ORC_BAD_HEADER;
+      return ORC_BAD_HEADER;
+    }
     const uint8_t* B = s + bo;
-    uint8_t ll[N_LL], lo[N_OFF];
-    for (int i = 0; i < N_LL; i++) ll[i] = (B[8 + (i >> 1)] >> (4 * (i & 1))) & 15;
-    for (int i = 0; i < N_OFF; i++) lo[i] = (B[168 + (i >> 1)] >> (4 * (i & 1))) & 15;
-    for (int i = 0; i < N_LL; i++) if (ll[i] > I.cwl) R->lengths_ok = 0;
-    for (int i = 0; i < N_OFF; i++) if (lo[i] > I.cwl) R->lengths_ok = 0;
-    uint64_t k1 = orc_kraft_scaled(ll, N_LL, (int)I.cwl), k2 = orc_kraft_scaled(lo, N_OFF, (int)I.cwl);
-    if (k1 != ((uint64_t)1 << I.cwl) || (k2 != 0 && k2 != ((uint64_t)1 << I.cwl))) R->kraft_ok = 0;
+    const int is_byte = !(I.flags & 2u);
+    if (!is_byte) {
+      uint8_t ll[N_LL], lo[N_OFF];
+      for (int i = 0; i < N_LL; i++) ll[i] = (B[8 + (i >> 1)] >> (4 * (i & 1))) & 15;
+      for (int i = 0; i < N_OFF; i++) lo[i] = (B[168 + (i >> 1)] >> (4 * (i & 1))) & 15;
+      for (int i = 0; i < N_LL; i++) if (ll[i] > I.cwl) R->lengths_ok = 0;
+      for (int i = 0; i < N_OFF; i++) if (lo[i] > I.cwl) R->lengths_ok = 0;
+      uint64_t k1 = orc_kraft_scaled(ll, N_LL, (int)I.cwl), k2 = orc_kraft_scaled(lo, N_OFF, (int)I.cwl);
+      if (k1 != ((uint64_t)1 << I.cwl) || (k2 != 0 && k2 != ((uint64_t)1 << I.cwl))) R->kraft_ok = 0;
+    }
     seqbuf S = {0};
     uint32_t ob;
     rc = block_tokens(s, len, &I, b, &S, &ob);
@@ -929,7 +1018,7 @@ int orc_validate(const uint8_t* s, uint64_t len, orc_report* R) {
        whole sequences whose stored sizes match their bits (block_tokens
        checked that).  Whether the runs are the even split of c5, ceil(n_seq
        / K) sequences each (this oracle's own choice), is reported apart. */
-    {
+    if (!is_byte) {
       uint64_t per = (S.n + I.n_sub - 1) / I.n_sub, left = S.n;
       for (uint32_t j = 0; j < I.n_sub; j++) {
         uint32_t ns = get32(B + BLK_FIXED + 12 * j + 8);

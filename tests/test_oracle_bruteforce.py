@@ -17,9 +17,10 @@ def _all_strings(alphabet, max_len):
 
 @pytest.mark.parametrize("alphabet,max_len", [("ab", 14), ("abc", 9)])
 @pytest.mark.parametrize("block_size", [16, 8])
-def test_every_tiny_input(alphabet, max_len, block_size):
-    p_mrr = oracle.params(block_size=block_size, n_sub=3, window=8)
-    p_de = oracle.params(block_size=block_size, n_sub=3, window=8, de=True)
+@pytest.mark.parametrize("byte_mode", [False, True])
+def test_every_tiny_input(alphabet, max_len, block_size, byte_mode):
+    p_mrr = oracle.params(block_size=block_size, n_sub=3, window=8, byte_mode=byte_mode)
+    p_de = oracle.params(block_size=block_size, n_sub=3, window=8, de=True, byte_mode=byte_mode)
     n_matches = 0
     for data in _all_strings(alphabet, max_len):
         arr = np.frombuffer(data, np.uint8)
@@ -28,7 +29,7 @@ def test_every_tiny_input(alphabet, max_len, block_size):
             assert bytes(oracle.decompress(s)) == data
             r = oracle.validate(s)
             assert r["rc"] == 0 and r["offsets_ok"] and r["kraft_ok"] and r["blocks_ok"] and r["mrr_ok"]
-            assert r["subblocks_ok"] and r["subblocks_even"]
+            assert r["subblocks_ok"] and (byte_mode or r["subblocks_even"])
             if p.de:
                 assert r["de_weak_ok"], data
             n_matches += r["n_matches"]

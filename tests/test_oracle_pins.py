@@ -285,3 +285,47 @@ def test_corruptions_are_reported():
         if oracle.decompress_status(bad) != oracle.OK:
             hits += 1
     assert hits >= 8
+
+
+# ---------------------------------------------------------------- Gompresso/Byte
+
+@pytest.mark.parametrize("name", ["text1m", "text256m", "csv1g"])
+def test_byte_mode_roundtrip_and_validators(name):
+    # Sec. 3.1 / 3.2: byte-level encoding without Huffman trees, same LZ77
+    w = datagen.WORKLOADS[name]
+    data = w.data(3 * w.block_size + 321)
+    for de in (False, True):
+        s = oracle.compress(data, oracle.params(w.block_size, 1, w.window, de=de, byte_mode=True))
+        info = oracle.stream_info(s)
+        assert not (info.flags & 2) and info.n_sub == 0 and info.cwl == 0
+        assert np.array_equal(oracle.decompress(s), data)
+        r = oracle.validate(s)
+        assert r["rc"] == 0 and r["offsets_ok"] and r["mrr_ok"] and r["blocks_ok"]
+        if de:
+            assert r["de_weak_ok"]
+
+
+def test_byte_record_layout_fig1():
+    # The Fig. 1 sequence (3 literals, copy of 3 bytes at distance 3) as one
+    # Byte record: literal length in bits 0-9, match code m = length - 2 in
+    # bits 10-15, distance - 1 in bits 16-31.
+    g = read_golden("fig1_lz77_example.txt")
+    ts = datagen.TokenStream(np.array(_ints(g["lit_len"]), np.uint32), np.array(_ints(g["mlen"]), np.uint32),
+                             np.array(_ints(g["off"]), np.uint32), np.frombuffer(g["lits"].encode(), np.uint8))
+    s = oracle.encode_tokens(ts, oracle.params(block_size=64, n_sub=1, window=8, byte_mode=True))
+    bo = int(s[64:72].view(np.uint64)[0])
+    n_seq, out_bytes, n_lit = (int(x) for x in s[bo:bo + 12].view(np.uint32))
+    assert (n_seq, out_bytes, n_lit) == (1, 6, 3)
+    assert int(s[bo + 16:bo + 20].view(np.uint32)[0]) == 3 | ((3 - 2) << 10) | ((3 - 1) << 16)
+    assert bytes(s[bo + 32:bo + 35]) == b"aac"
+    assert bytes(oracle.decompress(s)) == g["expect"].encode()
+
+
+def test_byte_mode_long_literal_runs():
+    rng = np.random.default_rng(12)
+    data = rng.integers(0, 256, 200_000).astype(np.uint8)  # incompressible: long literal runs
+    s = oracle.compress(data, oracle.params(65536, 1, 8192, byte_mode=True))
+    assert np.array_equal(oracle.decompress(s), data)
+    for b in range(oracle.stream_info(s).n_blocks):
+        t = oracle.block_tokens(s, b)
+        assert t.lit_len.max() <= 1023
