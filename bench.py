@@ -49,10 +49,12 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic_per_unit():
+def _traffic_per_unit(fmt: str = "bit"):
     """DRAM bytes per decompressed byte of the decode kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "decode_kernel_traffic.json")
+    ncu summary of the stream format, if it was taken on the current kernel
+    source."""
+    name = "decode_kernel_traffic.json" if fmt == "bit" else f"decode_kernel_traffic_{fmt}.json"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             t = json.load(f)
@@ -143,14 +145,17 @@ def _sum_over_ranks(dist, v: float) -> float:
     return float(t.item())
 
 
-def make_workload(name: str, size: int | None = None):
-    """(workload, data, {mode: stream}) using the product compressor."""
+def make_workload(name: str, size: int | None = None, fmt: str = "bit"):
+    """(workload, data, {mode: stream}) using the product compressor; fmt
+    "bit" writes Huffman blocks (Gompresso/Bit), "byte" byte-level blocks
+    (Gompresso/Byte)."""
     import paper_1606_00519_gb300 as gmp
     w = datagen.WORKLOADS[name]
     data = w.data(size)
     streams = {}
     for mode in ("mrr", "de"):
-        streams[mode] = gmp.compress(data, w.block_size, w.n_sub, w.window, de=(mode == "de"))
+        streams[mode] = gmp.compress(data, w.block_size, w.n_sub, w.window, de=(mode == "de"),
+                                     byte_mode=(fmt == "byte"))
     return w, data, streams
 
 
@@ -183,7 +188,7 @@ def run_reference(args):
     rank, world, local, dist = _dist_init(args)
     if rank != 0:
         return
-    w, data, streams = make_workload(args.workload, args.size)
+    w, data, streams = make_workload(args.workload, args.size, args.format)
     # each step decodes a bounded sample (the serial oracle is slow)
     per_step_blocks = args.ref_blocks
     for _ in range(args.warmup):
@@ -197,18 +202,22 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "decompressed GB/s", "value": gbs, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": _config(w, streams, data),
+            "data": "synthetic", "config": _config(w, streams, data, args.format),
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": f"per step: {desc}"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _config(w, streams, data):
+def _config(w, streams, data, fmt="bit"):
+    if fmt == "byte":
+        coding = "Gompresso/Byte (byte-level records, no Huffman)"
+    else:
+        coding = f"K={w.n_sub} sub-blocks"
     return {"workload": f"{w.name}: {w.size // MiB} MiB {w.kind}, {w.block_size // KiB} KiB blocks, "
-                        f"K={w.n_sub} sub-blocks, {w.window // KiB} KiB window, MRR and DE streams",
-            "bytes_per_stream": int(data.size), "block_size": w.block_size, "n_sub": w.n_sub,
-            "window": w.window, "cwl": 12,
+                        f"{coding}, {w.window // KiB} KiB window, MRR and DE streams",
+            "format": fmt, "bytes_per_stream": int(data.size), "block_size": w.block_size,
+            "n_sub": w.n_sub if fmt == "bit" else 0, "window": w.window, "cwl": 12 if fmt == "bit" else 0,
             "ratio_mrr": round(data.size / streams["mrr"].size, 4),
             "ratio_de": round(data.size / streams["de"].size, 4),
             "l2": "inputs larger than L2 (no flush)"}
@@ -221,7 +230,7 @@ def run_gmp(args):
     rank, world, local, dist = _dist_init(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w, data, streams = make_workload(args.workload, args.size)
+    w, data, streams = make_workload(args.workload, args.size, args.format)
     modes = ["mrr", "de"]
     ds = {m: gmp.DeviceStream(streams[m], device=dev) for m in modes}
     outs = {m: torch.empty(data.size, dtype=torch.uint8, device=dev) for m in modes}
@@ -331,12 +340,12 @@ def run_gmp(args):
     launch_avg_ms = float(np.mean(per_launch))
     algo_bytes = comp_bytes + out_bytes  # compressed read + decompressed written
     achieved = algo_bytes / (launch_avg_ms / 1e3) / 1e9
-    tpu, tinfo = _traffic_per_unit()
+    tpu, tinfo = _traffic_per_unit(args.format)
     line = {
         "metric": "decompressed GB/s", "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {**_config(w, streams, data), "parallelism": f"replicas x{world}",
+        "config": {**_config(w, streams, data, args.format), "parallelism": f"replicas x{world}",
                    "warps_per_cta": args.warps_per_cta or 4, "per_mode_gbs": per_mode,
                    "decode_kernel_cycles": phase_split},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
@@ -550,6 +559,8 @@ def main():
     ap.add_argument("--impl", default="gmp", choices=["gmp", "reference"])
     ap.add_argument("--workload", default="text256m", choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--size", type=int, default=None, help="override bytes per stream")
+    ap.add_argument("--format", default="bit", choices=["bit", "byte"],
+                    help="stream format: Huffman blocks (bit) or byte-level blocks (byte)")
     ap.add_argument("--warps-per-cta", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
     ap.add_argument("--ref-blocks", type=int, default=16, help="oracle blocks per reference step")

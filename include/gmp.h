@@ -9,7 +9,10 @@
  * the block's LZ77 sequences 32 at a time in one warp: two exclusive prefix
  * sums by shuffle, literal copy, then back-reference copy (Sec. 3.2.2), either
  * by Multi-Round Resolution (Fig. 5, Sec. 4.1) or, for streams written with
- * Dependency Elimination, in a single pass (Fig. 7, Sec. 4.2).
+ * Dependency Elimination, in a single pass (Fig. 7, Sec. 4.2).  Streams in
+ * the byte-level format (Gompresso/Byte, Sec. 3.1) skip the Huffman phase:
+ * the warp reads the block's fixed-size sequence records and literal bytes
+ * directly and resolves them the same way.
  *
  * Conventions for every function:
  *   - Return value: GMP_OK (0) or a negative gmp_error.  No exception crosses
@@ -32,14 +35,14 @@
  * their size in bits, and the bitstream; Sec. 3.1); the field layout is this
  * project's.
  *   File header, 64 bytes:
- *     0  "GMP1"            4  u16 version = 1      6  u16 flags (bit0 DE, bit1 Huffman = 1)
- *     8  u32 block_size   12  u16 n_sub (K, 1..64) 14 u8 cwl (1..12)  15 u8 0
+ *     0  "GMP1"            4  u16 version = 1      6  u16 flags (bit0 DE, bit1 Huffman)
+ *     8  u32 block_size   12  u16 n_sub (K, 1..64; Byte 0) 14 u8 cwl (1..12; Byte 0)  15 u8 0
  *    16  u32 window (1..32768)  20 u8 min_match = 3  21 u8 max_match (3..64)  22 u16 0
  *    24  u64 orig_size    32  u64 n_blocks         40 u64 stream_bytes   48 16 bytes 0
  *   Block offset table at 64: u64 per block, byte offset of the block from the
  *   start of the stream (a multiple of 16).  The stream ends with >= 16 zero
  *   bytes of padding.
- *   Block, at a 16-byte aligned offset:
+ *   Huffman block (Gompresso/Bit), at a 16-byte aligned offset:
  *     0  u32 n_seq   4 u32 out_bytes (block_size, except the last block)
  *     8  160 bytes: 4-bit code lengths of the 319 literal/length symbols
  *        (symbol s in byte s/2, low nibble for even s; 0 = unused)
@@ -62,6 +65,17 @@
  *   A sequence is a literal string followed by one back-reference (Sec. 3.2.2).
  *   Canonical codes (Sec. 3.1): codes of each length are consecutive in
  *   symbol order; the first code of length L is (first(L-1) + count(L-1)) << 1.
+ *   Byte blocks (Gompresso/Byte, Sec. 3.1: the sequences coded at byte
+ *   level, without Huffman trees, so that decoding is a plain read of the
+ *   records; file header flags bit1 = 0, n_sub = 0, cwl = 0):
+ *     0  u32 n_seq   4 u32 out_bytes   8 u32 n_lit (literal bytes)   12 u32 0
+ *    16  n_seq records, u32 each: bits 0-9 literal length (0..1023), bits
+ *        10-15 match code m (0 = no back-reference, 1..62 = match length
+ *        m + 2), bits 16-31 distance - 1
+ *   then, at the next 16-byte boundary, the n_lit literal bytes of the block
+ *   in sequence order, zero-padded to a 16-byte boundary.  Any sequence may
+ *   lack a back-reference (a literal string longer than 1023 bytes is written
+ *   as several sequences).
  *   DE flag: every back-reference of a 32-sequence group (numbered from the
  *   block start) reads only bytes produced before the group's copies start:
  *   bytes before the group, the group's literal strings, or earlier bytes of
@@ -146,6 +160,8 @@ typedef struct {
   uint32_t de;          /* 1: Dependency Elimination (Sec. 4.2), 0: plain (MRR) */
   uint32_t n_threads;   /* host threads, 0 = all cores */
   uint32_t lazy;        /* 1: one-step lazy match evaluation (default), 0: greedy */
+  uint32_t byte_mode;   /* 1: byte-level blocks (Gompresso/Byte, no Huffman; n_sub and cwl
+                           are ignored), 0: Huffman blocks (Gompresso/Bit, default) */
 } gmp_compress_opts;
 
 void gmp_compress_opts_default(gmp_compress_opts* o);

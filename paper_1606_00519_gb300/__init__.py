@@ -71,13 +71,14 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 
 def compress(data, block_size: int = 256 << 10, n_sub: int = 32, window: int = 32768, cwl: int = 12,
              max_match: int = 64, chain_depth: int = 64, de: bool = False, n_threads: int = 0,
-             lazy: bool = True) -> np.ndarray:
+             lazy: bool = True, byte_mode: bool = False) -> np.ndarray:
     """Compress host bytes into the stream format of include/gmp.h (host,
-    multi-threaded over blocks)."""
+    multi-threaded over blocks).  byte_mode: byte-level blocks (Gompresso/Byte,
+    no Huffman coding; n_sub and cwl do not apply)."""
     L = _native.lib()
     src = _np_bytes(data)
     o = CompressOpts(block_size, n_sub, window, cwl, max_match, chain_depth, 1 if de else 0, n_threads,
-                     1 if lazy else 0)
+                     1 if lazy else 0, 1 if byte_mode else 0)
     cap = L.gmp_compress_bound(src.size, ctypes.byref(o))
     out = np.empty(cap, np.uint8)
     n = ctypes.c_size_t()

@@ -93,7 +93,8 @@ class StreamInfo(ctypes.Structure):
 class CompressOpts(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("n_sub", ctypes.c_uint32), ("window", ctypes.c_uint32),
                 ("cwl", ctypes.c_uint32), ("max_match", ctypes.c_uint32), ("chain_depth", ctypes.c_uint32),
-                ("de", ctypes.c_uint32), ("n_threads", ctypes.c_uint32), ("lazy", ctypes.c_uint32)]
+                ("de", ctypes.c_uint32), ("n_threads", ctypes.c_uint32), ("lazy", ctypes.c_uint32),
+                ("byte_mode", ctypes.c_uint32)]
 
 
 class ContextOpts(ctypes.Structure):

@@ -8,7 +8,9 @@
 // Code lengths come from an ordinary Huffman merge followed by a Kraft repair
 // that lengthens rarely used codes until the code fits in cwl bits and then
 // shortens frequent ones until the Kraft sum is exactly one (the decoder needs
-// a complete code).  Any valid stream decodes to the same bytes, so this
+// a complete code).  With byte_mode the same parse is written as fixed
+// 4-byte records and raw literals (Gompresso/Byte, Sec. 3.1) instead of
+// Huffman bitstreams.  Any valid stream decodes to the same bytes, so this
 // compressor's choices need not match any other encoder's.
 #include <stdint.h>
 #include <string.h>
@@ -27,6 +29,7 @@ namespace {
 
 constexpr int kHashBits = 16;
 constexpr uint32_t kNil = 0xffffffffu;
+constexpr uint32_t kByteMaxLit = 1023;  // literal length field of a Byte record (10 bits)
 
 struct Seq {
   uint32_t lit_start, lit_len, mlen, dist;
@@ -116,6 +119,21 @@ void parse_block(const uint8_t* in, uint32_t n, const gmp_compress_opts& o, std:
       }
     }
     if (len) {
+      if (o.byte_mode) {
+        // a Byte record holds at most 1023 literals: longer literal strings
+        // are cut into literal-only sequences, members of their DE group like
+        // any other sequence.  (The match was searched before the cut was
+        // known; the cut can only move it into a later group, whose earlier
+        // back-references are a subset of the ones it avoided.)
+        while (i - lit_start > kByteMaxLit) {
+          seqs.push_back(Seq{lit_start, kByteMaxLit, 0, 0});
+          lit_start += kByteMaxLit;
+          if (o.de) {
+            grp_lo[in_grp] = grp_hi[in_grp] = 0;  // no back-reference
+            if (++in_grp == 32) in_grp = 0;
+          }
+        }
+      }
       seqs.push_back(Seq{lit_start, i - lit_start, len, dist});
       if (o.de) {
         grp_lo[in_grp] = i;
@@ -128,6 +146,8 @@ void parse_block(const uint8_t* in, uint32_t n, const gmp_compress_opts& o, std:
       i++;
     }
   }
+  if (o.byte_mode)
+    for (; n - lit_start > kByteMaxLit; lit_start += kByteMaxLit) seqs.push_back(Seq{lit_start, kByteMaxLit, 0, 0});
   if (lit_start < n) seqs.push_back(Seq{lit_start, n - lit_start, 0, 0});
 }
 
@@ -324,6 +344,29 @@ void encode_block(const uint8_t* in, uint32_t n, const std::vector<Seq>& seqs, c
   bs.finish();
 }
 
+// Encode one block in the byte-level format (Gompresso/Byte, Sec. 3.1):
+// header {n_seq, out_bytes, n_lit, 0}, one 4-byte record per sequence
+// (literal length | (match length - 2) << 10 | (distance - 1) << 16; match
+// code 0 when the sequence has no back-reference), zero padding to 16 bytes,
+// the block's literal bytes in order, zero padding to 16 bytes.
+void encode_block_byte(const uint8_t* in, uint32_t n, const std::vector<Seq>& seqs, std::vector<uint8_t>& blk) {
+  uint64_t n_lit = 0;
+  for (const Seq& q : seqs) n_lit += q.lit_len;
+  const size_t rec_end = (16 + 4 * seqs.size() + 15) & ~size_t(15);
+  blk.assign(rec_end + ((n_lit + 15) & ~uint64_t(15)), 0);
+  put_le(&blk[0], seqs.size(), 4);
+  put_le(&blk[4], n, 4);
+  put_le(&blk[8], n_lit, 4);
+  size_t lp = rec_end;
+  for (size_t k = 0; k < seqs.size(); k++) {
+    const Seq& q = seqs[k];
+    const uint32_t rec = q.lit_len | (q.mlen ? ((q.mlen - 2) << 10) | ((q.dist - 1) << 16) : 0u);
+    put_le(&blk[16 + 4 * k], rec, 4);
+    memcpy(&blk[lp], in + q.lit_start, q.lit_len);
+    lp += q.lit_len;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -338,11 +381,14 @@ void gmp_compress_opts_default(gmp_compress_opts* o) {
   o->de = 0;
   o->n_threads = 0;
   o->lazy = 1;
+  o->byte_mode = 0;
 }
 
 size_t gmp_compress_bound(size_t n, const gmp_compress_opts* o) {
   if (!o || o->block_size == 0) return 0;
   size_t nb = (n + o->block_size - 1) / o->block_size;
+  // Byte blocks: at most one 4-byte record per byte plus the literals
+  if (o->byte_mode) return gmp::kHeaderBytes + 8 * nb + 16 + nb * 48 + 5 * n + 32;
   size_t per_block = ((gmp::kBlockFixed + 12 * (size_t)o->n_sub + 15) & ~size_t(15)) + 32;
   return gmp::kHeaderBytes + 8 * nb + 16 + nb * per_block + (n * 12 + 7) / 8 + 2 * nb + 32;
 }
@@ -351,9 +397,10 @@ int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* opts, v
                  size_t* out_bytes) {
   if ((!host_in && n) || !opts || !host_out || !out_bytes) return GMP_ERR_INVALID_ARG;
   gmp_compress_opts o = *opts;
-  if (o.block_size == 0 || o.n_sub == 0 || o.n_sub > gmp::kMaxSub || o.window == 0 || o.window > 32768 || o.cwl == 0 ||
-      o.cwl > 12 || o.cwl < 9 || o.max_match < 3 || o.max_match > 64 || o.chain_depth == 0)
+  if (o.block_size == 0 || o.window == 0 || o.window > 32768 || o.max_match < 3 || o.max_match > 64 ||
+      o.chain_depth == 0 || o.byte_mode > 1)
     return GMP_ERR_INVALID_ARG;
+  if (!o.byte_mode && (o.n_sub == 0 || o.n_sub > gmp::kMaxSub || o.cwl < 9 || o.cwl > 12)) return GMP_ERR_INVALID_ARG;
   const uint8_t* in = static_cast<const uint8_t*>(host_in);
   const size_t nb = (n + o.block_size - 1) / o.block_size;
   std::vector<std::vector<uint8_t>> blocks;
@@ -376,7 +423,8 @@ int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* opts, v
         size_t s = b * (size_t)o.block_size;
         uint32_t len = (uint32_t)std::min<size_t>(o.block_size, n - s);
         parse_block(in + s, len, o, seqs, head, chain);
-        encode_block(in + s, len, seqs, o, blocks[b]);
+        if (o.byte_mode) encode_block_byte(in + s, len, seqs, blocks[b]);
+        else encode_block(in + s, len, seqs, o, blocks[b]);
       }
     } catch (...) {
       failed = true;
@@ -396,10 +444,10 @@ int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* opts, v
   memset(out, 0, pos);
   memcpy(out, "GMP1", 4);
   put_le(out + 4, GMP_VERSION, 2);
-  put_le(out + 6, (o.de ? 1u : 0u) | 2u, 2);
+  put_le(out + 6, (o.de ? 1u : 0u) | (o.byte_mode ? 0u : 2u), 2);
   put_le(out + 8, o.block_size, 4);
-  put_le(out + 12, o.n_sub, 2);
-  out[14] = (uint8_t)o.cwl;
+  put_le(out + 12, o.byte_mode ? 0u : o.n_sub, 2);
+  out[14] = (uint8_t)(o.byte_mode ? 0u : o.cwl);
   put_le(out + 16, o.window, 4);
   out[20] = 3;
   out[21] = (uint8_t)o.max_match;

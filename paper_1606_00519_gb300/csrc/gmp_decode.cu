@@ -24,6 +24,10 @@
 //  caller's buffer with coalesced 16-byte stores, so every output byte is
 //  written to device memory once.
 //
+//  Byte blocks (Gompresso/Byte, Sec. 3.1) have no phase A: their sequence
+//  records and literal bytes are read by phase B straight from the stream,
+//  with each group's records checked before it is staged or copied.
+//
 // MRR reading (the printed algorithm is ambiguous, see the comment at
 // resolve_mrr_global): HWM = write position of the lowest pending lane; a lane may
 // copy once min(read_pos + length, write_pos) <= HWM.
@@ -403,6 +407,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   // ---- stream header (64 bytes), block reference
   int err = 0;
   uint32_t flags = 0, K = 0, window = 0, max_match = 0;
+  bool byte_fmt = false;  // Gompresso/Byte block: records and raw literals, no Huffman phase
   if (F.comp_bytes < 64 || (((uintptr_t)comp) & 15u)) {
     if (lane == 0) set_status(status, GMP_STATUS_BAD_HEADER);
     return;
@@ -417,8 +422,11 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     K = w3 & 0xffffu;
     uint32_t cwl = (w3 >> 16) & 0xffu;
     max_match = (w5 >> 8) & 0xffu;
-    if (magic != 0x31504d47u || (w1 & 0xffffu) != 1u || !(flags & 2u) || K == 0 || K > MAX_SUB || cwl == 0 ||
-        cwl > 12 || window == 0 || window > 32768 || (w5 & 0xffu) != 3u || max_match < 3 || max_match > 64)
+    byte_fmt = !(flags & 2u);
+    if (magic != 0x31504d47u || (w1 & 0xffffu) != 1u || flags > 3u || window == 0 || window > 32768 ||
+        (w5 & 0xffu) != 3u || max_match < 3 || max_match > 64)
+      err = GMP_STATUS_BAD_HEADER;
+    else if (byte_fmt ? (K != 0 || cwl != 0) : (K == 0 || K > MAX_SUB || cwl == 0 || cwl > 12))
       err = GMP_STATUS_BAD_HEADER;
   }
   const gmp_block_ref br = F.index[b];
@@ -426,7 +434,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     if ((br.comp_offset & 15) || br.comp_offset > F.comp_bytes || br.comp_bytes > F.comp_bytes - br.comp_offset ||
         br.out_offset > F.out_cap || br.out_bytes > F.out_cap - br.out_offset)
       err = GMP_STATUS_OUTPUT_OVERRUN;
-    else if (br.comp_bytes < 192 + 12ull * K)
+    else if (br.comp_bytes < (byte_fmt ? 16ull : 192 + 12ull * K))
       err = GMP_STATUS_BAD_HEADER;
   }
   if (err) {
@@ -436,226 +444,256 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   const uint8_t* B = comp + br.comp_offset;
   const uint32_t n_seq = ld_u32_nc(B);
   const uint32_t out_bytes = ld_u32_nc(B + 4);
-  if (out_bytes != br.out_bytes) err = GMP_STATUS_BAD_HEADER;
-  else if (out_bytes > P.max_out || n_seq > P.max_seq) err = GMP_STATUS_CAPACITY;
-  if (err) {
-    if (lane == 0) set_status(status, err);
-    return;
-  }
-  const uint32_t bs_off = (192u + 12u * K + 15u) & ~15u;  // bitstream start within the block
-  const uint64_t bits_avail = (br.comp_bytes - bs_off) * 8ull;
-
-  // ---- sub-block table: prefix sums of bit sizes, output sizes, sequences
-  {
-    uint32_t carry_bit = 0, carry_out = 0, carry_seq = 0;
-    for (uint32_t base = 0; base < K; base += 32) {
-      uint32_t j = base + lane;
-      uint32_t nb = 0, no = 0, ns = 0;
-      if (j < K) {
-        const uint8_t* e = B + 192 + 12 * j;
-        nb = ld_u32_nc(e);
-        no = ld_u32_nc(e + 4);
-        ns = ld_u32_nc(e + 8);
-      }
-      uint32_t ib = warp_incl_scan(nb), io = warp_incl_scan(no), is = warp_incl_scan(ns);
-      if (j < K) {
-        S.sb_bit[j] = carry_bit + ib - nb;
-        S.sb_bits[j] = nb;
-        S.sb_out[j] = carry_out + io - no;
-        S.sb_outn[j] = no;
-        S.sb_seq[j] = carry_seq + is - ns;
-        S.sb_seqn[j] = ns;
-      }
-      // sizes are checked below against 64-bit totals, so a wrapped 32-bit
-      // sum cannot pass: the totals are bounded by out_bytes / n_seq.
-      carry_bit += __shfl_sync(FULL, ib, 31);
-      carry_out += __shfl_sync(FULL, io, 31);
-      carry_seq += __shfl_sync(FULL, is, 31);
-    }
-    if (lane == 0) S.sb_seq[K] = carry_seq;
-    // overflow-safe totals
-    uint64_t tb = 0, to = 0, ts = 0;
-    for (uint32_t j = lane; j < K; j += 32) {
-      const uint8_t* e = B + 192 + 12 * j;
-      tb += ld_u32_nc(e);
-      to += ld_u32_nc(e + 4);
-      ts += ld_u32_nc(e + 8);
-    }
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-      tb += __shfl_xor_sync(FULL, tb, d);
-      to += __shfl_xor_sync(FULL, to, d);
-      ts += __shfl_xor_sync(FULL, ts, d);
-    }
-    if (ts != n_seq || to != out_bytes) err = GMP_STATUS_BAD_HEADER;
-    else if (tb > bits_avail) err = GMP_STATUS_BITSTREAM;
+  // Byte blocks: literal count and the literal section's offset in the block
+  uint32_t n_lit = 0;
+  uint64_t lit_off = 0;
+  if (out_bytes != br.out_bytes) {
+    err = GMP_STATUS_BAD_HEADER;
+  } else if (byte_fmt) {
+    // the records and the padded literal section lie inside the block (whole
+    // 16-byte chunks, which the literal staging reads)
+    n_lit = ld_u32_nc(B + 8);
+    lit_off = (16ull + 4ull * n_seq + 15ull) & ~15ull;
+    if (lit_off + ((n_lit + 15ull) & ~15ull) > br.comp_bytes) err = GMP_STATUS_BAD_HEADER;
+  } else if (out_bytes > P.max_out || n_seq > P.max_seq) {
+    err = GMP_STATUS_CAPACITY;
   }
   if (err) {
     if (lane == 0) set_status(status, err);
     return;
   }
-
-  // ---- code lengths and lookup tables (Sec. 3.2.1)
-  for (uint32_t i = lane; i < (uint32_t)(N_LL + N_OFF); i += 32) {
-    uint32_t sym = i < (uint32_t)N_LL ? i : i - N_LL;
-    uint32_t byte = i < (uint32_t)N_LL ? 8 + (sym >> 1) : 168 + (sym >> 1);
-    uint8_t v = __ldg(B + byte);
-    S.lens[i] = (sym & 1) ? (v >> 4) : (v & 15);
-  }
-  __syncwarp();
-  bool ok1 = build_lut<LUT_BITS>(S, S.lens, N_LL, S.u.lut.ll);
-  // the offset tree is built last, so its canonical arrays stay in S for
-  // decode_long
-  bool ok2 = build_lut<OFF_BITS>(S, S.lens + N_LL, N_OFF, S.u.lut.off);
-  if (!ok1 || !ok2) {
-    if (lane == 0) set_status(status, GMP_STATUS_BAD_HEADER);
-    return;
-  }
-
-  const long long t_tables = clock64();
-  // ---- Phase A: lane per sub-block Huffman decode (Sec. 3.2.1)
-  // Every lane of the warp takes one symbol per step (a literal, or a length
-  // followed by its offset), with the literal / back-reference work done under
-  // predicates and the lanes reconverged after each step, so the warp issues
-  // one instruction stream for all 32 sub-blocks.
+  // phase A output (Huffman blocks): records and the literal shadow in the
+  // warp's scratch slot
   uint2* rec = reinterpret_cast<uint2*>(slot);
   uint8_t* shadow = slot + P.shadow_off;
-  const uint8_t* bs = B + bs_off;
-  // 16-byte chunks of the block's bitstream; chunks past the block read as 0
-  const uint64_t bs_chunks = (br.comp_bytes - bs_off) / 16;
-  auto ld4 = [&](uint32_t c) -> uint4 {
-    return (uint64_t)c < bs_chunks ? __ldg(reinterpret_cast<const uint4*>(bs) + c) : make_uint4(0, 0, 0, 0);
-  };
-  for (uint32_t jb = 0; jb < K; jb += 32) {
-    const uint32_t j = jb + lane;
-    bool act = j < K;
-    uint32_t pos = 0, end = 0, outp = 0, out_end = 0, lit_dst = 0, lit_lim = 0, nlit = 0, q = 0, q_end = 0;
-    uint32_t lit_run = 0;
-    // bit buffer (nb valid bits), a stash of up to 4 words (lo, hi) and the
-    // next 16-byte chunk, loaded one chunk ahead of use
-    uint64_t buf = 0, lo = 0, hi = 0;
-    int nb = 0;
-    uint32_t scnt = 0, ci = 0;
-    uint4 pre = make_uint4(0, 0, 0, 0);
-    auto next_word = [&]() -> uint32_t {
-      if (scnt == 0) {
-        lo = (uint64_t)pre.x | ((uint64_t)pre.y << 32);
-        hi = (uint64_t)pre.z | ((uint64_t)pre.w << 32);
-        scnt = 4;
-        pre = ld4(ci++);
+  const uint8_t* lits = shadow;  // phase B's literal source
+  long long t_tables, t_phase_a;
+  if (byte_fmt) {
+    // one run of sequences: phase B reads the records from the stream and
+    // the literals from the block's literal section
+    if (lane == 0) {
+      S.sb_seq[0] = 0;
+      S.sb_seq[1] = n_seq;
+      S.sb_lit[0] = 0;
+    }
+    K = 1;
+    lits = B + lit_off;
+    t_tables = t_phase_a = clock64();
+    __syncwarp();
+  } else {
+    const uint32_t bs_off = (192u + 12u * K + 15u) & ~15u;  // bitstream start within the block
+    const uint64_t bits_avail = (br.comp_bytes - bs_off) * 8ull;
+
+    // ---- sub-block table: prefix sums of bit sizes, output sizes, sequences
+    {
+      uint32_t carry_bit = 0, carry_out = 0, carry_seq = 0;
+      for (uint32_t base = 0; base < K; base += 32) {
+        uint32_t j = base + lane;
+        uint32_t nb = 0, no = 0, ns = 0;
+        if (j < K) {
+          const uint8_t* e = B + 192 + 12 * j;
+          nb = ld_u32_nc(e);
+          no = ld_u32_nc(e + 4);
+          ns = ld_u32_nc(e + 8);
+        }
+        uint32_t ib = warp_incl_scan(nb), io = warp_incl_scan(no), is = warp_incl_scan(ns);
+        if (j < K) {
+          S.sb_bit[j] = carry_bit + ib - nb;
+          S.sb_bits[j] = nb;
+          S.sb_out[j] = carry_out + io - no;
+          S.sb_outn[j] = no;
+          S.sb_seq[j] = carry_seq + is - ns;
+          S.sb_seqn[j] = ns;
+        }
+        // sizes are checked below against 64-bit totals, so a wrapped 32-bit
+        // sum cannot pass: the totals are bounded by out_bytes / n_seq.
+        carry_bit += __shfl_sync(FULL, ib, 31);
+        carry_out += __shfl_sync(FULL, io, 31);
+        carry_seq += __shfl_sync(FULL, is, 31);
       }
-      const uint32_t w = (uint32_t)lo;
-      lo = (lo >> 32) | (hi << 32);
-      hi >>= 32;
-      scnt--;
-      return w;
+      if (lane == 0) S.sb_seq[K] = carry_seq;
+      // overflow-safe totals
+      uint64_t tb = 0, to = 0, ts = 0;
+      for (uint32_t j = lane; j < K; j += 32) {
+        const uint8_t* e = B + 192 + 12 * j;
+        tb += ld_u32_nc(e);
+        to += ld_u32_nc(e + 4);
+        ts += ld_u32_nc(e + 8);
+      }
+  #pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) {
+        tb += __shfl_xor_sync(FULL, tb, d);
+        to += __shfl_xor_sync(FULL, to, d);
+        ts += __shfl_xor_sync(FULL, ts, d);
+      }
+      if (ts != n_seq || to != out_bytes) err = GMP_STATUS_BAD_HEADER;
+      else if (tb > bits_avail) err = GMP_STATUS_BITSTREAM;
+    }
+    if (err) {
+      if (lane == 0) set_status(status, err);
+      return;
+    }
+
+    // ---- code lengths and lookup tables (Sec. 3.2.1)
+    for (uint32_t i = lane; i < (uint32_t)(N_LL + N_OFF); i += 32) {
+      uint32_t sym = i < (uint32_t)N_LL ? i : i - N_LL;
+      uint32_t byte = i < (uint32_t)N_LL ? 8 + (sym >> 1) : 168 + (sym >> 1);
+      uint8_t v = __ldg(B + byte);
+      S.lens[i] = (sym & 1) ? (v >> 4) : (v & 15);
+    }
+    __syncwarp();
+    bool ok1 = build_lut<LUT_BITS>(S, S.lens, N_LL, S.u.lut.ll);
+    // the offset tree is built last, so its canonical arrays stay in S for
+    // decode_long
+    bool ok2 = build_lut<OFF_BITS>(S, S.lens + N_LL, N_OFF, S.u.lut.off);
+    if (!ok1 || !ok2) {
+      if (lane == 0) set_status(status, GMP_STATUS_BAD_HEADER);
+      return;
+    }
+
+    t_tables = clock64();
+    // ---- Phase A: lane per sub-block Huffman decode (Sec. 3.2.1)
+    // Every lane of the warp takes one symbol per step (a literal, or a length
+    // followed by its offset), with the literal / back-reference work done under
+    // predicates and the lanes reconverged after each step, so the warp issues
+    // one instruction stream for all 32 sub-blocks.
+    const uint8_t* bs = B + bs_off;
+    // 16-byte chunks of the block's bitstream; chunks past the block read as 0
+    const uint64_t bs_chunks = (br.comp_bytes - bs_off) / 16;
+    auto ld4 = [&](uint32_t c) -> uint4 {
+      return (uint64_t)c < bs_chunks ? __ldg(reinterpret_cast<const uint4*>(bs) + c) : make_uint4(0, 0, 0, 0);
     };
-    if (act) {
-      pos = S.sb_bit[j];
-      end = pos + S.sb_bits[j];
-      // the stash starts with chunk c0 minus the words before the start word
-      const uint32_t w0 = pos >> 5, c0 = w0 >> 2;
-      const uint4 c = ld4(c0);
-      lo = (uint64_t)c.x | ((uint64_t)c.y << 32);
-      hi = (uint64_t)c.z | ((uint64_t)c.w << 32);
-      for (uint32_t k = 0; k < (w0 & 3u); k++) {
+    for (uint32_t jb = 0; jb < K; jb += 32) {
+      const uint32_t j = jb + lane;
+      bool act = j < K;
+      uint32_t pos = 0, end = 0, outp = 0, out_end = 0, lit_dst = 0, lit_lim = 0, nlit = 0, q = 0, q_end = 0;
+      uint32_t lit_run = 0;
+      // bit buffer (nb valid bits), a stash of up to 4 words (lo, hi) and the
+      // next 16-byte chunk, loaded one chunk ahead of use
+      uint64_t buf = 0, lo = 0, hi = 0;
+      int nb = 0;
+      uint32_t scnt = 0, ci = 0;
+      uint4 pre = make_uint4(0, 0, 0, 0);
+      auto next_word = [&]() -> uint32_t {
+        if (scnt == 0) {
+          lo = (uint64_t)pre.x | ((uint64_t)pre.y << 32);
+          hi = (uint64_t)pre.z | ((uint64_t)pre.w << 32);
+          scnt = 4;
+          pre = ld4(ci++);
+        }
+        const uint32_t w = (uint32_t)lo;
         lo = (lo >> 32) | (hi << 32);
         hi >>= 32;
-      }
-      scnt = 4u - (w0 & 3u);
-      pre = ld4(c0 + 1);
-      ci = c0 + 2;
-      buf = (uint64_t)(next_word() >> (pos & 31u));
-      nb = 32 - (int)(pos & 31u);
-      buf |= (uint64_t)next_word() << nb;
-      nb += 32;
-      outp = S.sb_out[j];
-      out_end = outp + S.sb_outn[j];
-      lit_dst = ((S.sb_out[j] + 15u) & ~15u) + 16u * j;
-      lit_lim = lit_dst + S.sb_outn[j];  // first byte past the lane's literal region
-      q = S.sb_seq[j];
-      q_end = q + S.sb_seqn[j];
-      act = q < q_end;
-    }
-    while (__any_sync(FULL, act)) {
-#ifdef GMP_PHASE_TIMERS
-      tdet[5]++;
-#endif
+        scnt--;
+        return w;
+      };
       if (act) {
-        if (nb < 32) {
-          buf |= (uint64_t)next_word() << nb;
-          nb += 32;
+        pos = S.sb_bit[j];
+        end = pos + S.sb_bits[j];
+        // the stash starts with chunk c0 minus the words before the start word
+        const uint32_t w0 = pos >> 5, c0 = w0 >> 2;
+        const uint4 c = ld4(c0);
+        lo = (uint64_t)c.x | ((uint64_t)c.y << 32);
+        hi = (uint64_t)c.z | ((uint64_t)c.w << 32);
+        for (uint32_t k = 0; k < (w0 & 3u); k++) {
+          lo = (lo >> 32) | (hi << 32);
+          hi >>= 32;
         }
-        const uint32_t e = S.u.lut.ll[buf & (LUT_SIZE - 1)];
-        const uint32_t L = e >> 9, sym = e & 511u;
-        buf >>= L;
-        nb -= (int)L;
-        pos += L;
-        if (sym < 256) {
-          shadow[min(lit_dst + nlit, lit_lim)] = (uint8_t)sym;  // clamped: a corrupt stream is caught below
-          nlit++;
-          lit_run++;
-          outp++;
-        } else {
-          uint32_t ml = 0, dist = 0;
-          if (sym > 256) {
-            ml = sym - 254u;
-            if (nb < 32) {
-              buf |= (uint64_t)next_word() << nb;
-              nb += 32;
-            }
-            uint32_t e2 = S.u.lut.off[buf & (OFF_SIZE - 1)];
-            if (e2 == LONG_CODE) e2 = decode_long<OFF_BITS>(S, (uint32_t)buf & (LUT_SIZE - 1));
-            const uint32_t L2 = e2 >> 9, os = e2 & 31u;
-            const uint32_t ne = os < 4 ? 0u : (os >> 1) - 1u;
-            const uint32_t extra = (uint32_t)(buf >> L2) & ((1u << ne) - 1u);
-            buf >>= L2 + ne;
-            nb -= (int)(L2 + ne);
-            pos += L2 + ne;
-            dist = os < 4 ? os + 1u : ((2u | (os & 1u)) << ne) + extra + 1u;
-            if (L2 == 0 || os >= (uint32_t)N_OFF || ml > max_match) err = GMP_STATUS_CORRUPT_SYMBOL;
-            else if (dist > window || dist > outp) err = GMP_STATUS_BAD_OFFSET;
-            else if (ml > out_end - min(outp, out_end)) err = GMP_STATUS_OUTPUT_OVERRUN;
-          } else if (q + 1 != n_seq) {
-            err = GMP_STATUS_CORRUPT_SYMBOL;  // the end symbol only closes the block's last sequence
-          }
-          rec[q] = make_uint2(lit_run, (dist << 8) | ml);
-          q++;
-          lit_run = 0;
-          outp += ml;
-        }
-        // a lane that runs past its sub-block stops here (this bounds the
-        // loop on corrupt input); sizes are checked when the sub-block ends
-        if (L == 0) err = GMP_STATUS_CORRUPT_SYMBOL;
-        else if (pos > end) err = GMP_STATUS_BITSTREAM;
-        act = !err && q < q_end;
+        scnt = 4u - (w0 & 3u);
+        pre = ld4(c0 + 1);
+        ci = c0 + 2;
+        buf = (uint64_t)(next_word() >> (pos & 31u));
+        nb = 32 - (int)(pos & 31u);
+        buf |= (uint64_t)next_word() << nb;
+        nb += 32;
+        outp = S.sb_out[j];
+        out_end = outp + S.sb_outn[j];
+        lit_dst = ((S.sb_out[j] + 15u) & ~15u) + 16u * j;
+        lit_lim = lit_dst + S.sb_outn[j];  // first byte past the lane's literal region
+        q = S.sb_seq[j];
+        q_end = q + S.sb_seqn[j];
+        act = q < q_end;
       }
-      __syncwarp();
+      while (__any_sync(FULL, act)) {
+  #ifdef GMP_PHASE_TIMERS
+        tdet[5]++;
+  #endif
+        if (act) {
+          if (nb < 32) {
+            buf |= (uint64_t)next_word() << nb;
+            nb += 32;
+          }
+          const uint32_t e = S.u.lut.ll[buf & (LUT_SIZE - 1)];
+          const uint32_t L = e >> 9, sym = e & 511u;
+          buf >>= L;
+          nb -= (int)L;
+          pos += L;
+          if (sym < 256) {
+            shadow[min(lit_dst + nlit, lit_lim)] = (uint8_t)sym;  // clamped: a corrupt stream is caught below
+            nlit++;
+            lit_run++;
+            outp++;
+          } else {
+            uint32_t ml = 0, dist = 0;
+            if (sym > 256) {
+              ml = sym - 254u;
+              if (nb < 32) {
+                buf |= (uint64_t)next_word() << nb;
+                nb += 32;
+              }
+              uint32_t e2 = S.u.lut.off[buf & (OFF_SIZE - 1)];
+              if (e2 == LONG_CODE) e2 = decode_long<OFF_BITS>(S, (uint32_t)buf & (LUT_SIZE - 1));
+              const uint32_t L2 = e2 >> 9, os = e2 & 31u;
+              const uint32_t ne = os < 4 ? 0u : (os >> 1) - 1u;
+              const uint32_t extra = (uint32_t)(buf >> L2) & ((1u << ne) - 1u);
+              buf >>= L2 + ne;
+              nb -= (int)(L2 + ne);
+              pos += L2 + ne;
+              dist = os < 4 ? os + 1u : ((2u | (os & 1u)) << ne) + extra + 1u;
+              if (L2 == 0 || os >= (uint32_t)N_OFF || ml > max_match) err = GMP_STATUS_CORRUPT_SYMBOL;
+              else if (dist > window || dist > outp) err = GMP_STATUS_BAD_OFFSET;
+              else if (ml > out_end - min(outp, out_end)) err = GMP_STATUS_OUTPUT_OVERRUN;
+            } else if (q + 1 != n_seq) {
+              err = GMP_STATUS_CORRUPT_SYMBOL;  // the end symbol only closes the block's last sequence
+            }
+            rec[q] = make_uint2(lit_run, (dist << 8) | ml);
+            q++;
+            lit_run = 0;
+            outp += ml;
+          }
+          // a lane that runs past its sub-block stops here (this bounds the
+          // loop on corrupt input); sizes are checked when the sub-block ends
+          if (L == 0) err = GMP_STATUS_CORRUPT_SYMBOL;
+          else if (pos > end) err = GMP_STATUS_BITSTREAM;
+          act = !err && q < q_end;
+        }
+        __syncwarp();
+      }
+      if (j < K) {
+        if (!err && pos != end) err = GMP_STATUS_BITSTREAM;
+        if (!err && outp != out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
+        S.sb_lit[j] = nlit;
+      }
     }
-    if (j < K) {
-      if (!err && pos != end) err = GMP_STATUS_BITSTREAM;
-      if (!err && outp != out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
-      S.sb_lit[j] = nlit;
-    }
-  }
-  if (err) set_status(status, err);
-  if (__ballot_sync(FULL, err != 0)) return;
-  __syncwarp();  // phase A's records and literals are visible to the whole warp
+    if (err) set_status(status, err);
+    if (__ballot_sync(FULL, err != 0)) return;
+    __syncwarp();  // phase A's records and literals are visible to the whole warp
 
-  // literal-source delta per sub-block: shadow start minus literals before it
-  {
-    uint32_t carry = 0;
-    for (uint32_t base = 0; base < K; base += 32) {
-      uint32_t j = base + lane;
-      uint32_t n = j < K ? S.sb_lit[j] : 0u;
-      uint32_t inc = warp_incl_scan(n);
-      if (j < K) S.sb_lit[j] = (((S.sb_out[j] + 15u) & ~15u) + 16u * j) - (carry + inc - n);
-      carry += __shfl_sync(FULL, inc, 31);
+    // literal-source delta per sub-block: shadow start minus literals before it
+    {
+      uint32_t carry = 0;
+      for (uint32_t base = 0; base < K; base += 32) {
+        uint32_t j = base + lane;
+        uint32_t n = j < K ? S.sb_lit[j] : 0u;
+        uint32_t inc = warp_incl_scan(n);
+        if (j < K) S.sb_lit[j] = (((S.sb_out[j] + 15u) & ~15u) + 16u * j) - (carry + inc - n);
+        carry += __shfl_sync(FULL, inc, 31);
+      }
     }
-  }
-  __syncwarp();
+    __syncwarp();
+    t_phase_a = clock64();
+  }  // Huffman blocks
 
-  const long long t_phase_a = clock64();
   // ---- Phase B: 32 sequences per step (Sec. 3.2.2)
   // Group g+1 is prepared while group g runs: its two prefix sums are taken
   // and its literal runs and far back-reference sources are copied into the
@@ -671,7 +709,16 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
 
   struct Prep {
     uint32_t ll, ml, dst, lsrc, wpos, rpos, gtot, glits, jnext, far_lo, far_hi, lit_lo, lpre;
+    int err;  // Byte blocks: the group's records failed a check (a gmp_status)
     bool valid, lit_staged;
+  };
+  // sequence t as {literal length, (distance << 8) | match length}; 0 past the end
+  auto load_rec = [&](uint32_t t) -> uint2 {
+    if (t >= n_seq) return make_uint2(0, 0);
+    if (!byte_fmt) return rec[t];
+    // match code 63 has no length; it decodes as 65 > max_match and is caught in prep
+    const uint32_t r = ld_u32_nc(B + 16 + 4ull * t), m = (r >> 10) & 63u;
+    return make_uint2(r & 1023u, m ? ((((r >> 16) + 1u) << 8) | (m + 2u)) : 0u);
   };
   // prefix sums and staging of group h; G0h / litposh / jc: where it starts
   auto prep = [&](uint32_t h, uint2 r, uint32_t G0h, uint32_t litposh, uint32_t jc, bool allow, int stage) {
@@ -713,6 +760,16 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     q.far_lo = q.far_hi = 0;
     q.lit_lo = 0;
     q.lit_staged = false;
+    q.err = 0;
+    if (byte_fmt) {
+      // phase A checks Huffman records as it decodes them; Byte records are
+      // checked here, before anything is staged or copied for the group
+      if (__any_sync(FULL, q.ml > max_match)) q.err = GMP_STATUS_CORRUPT_SYMBOL;
+      else if (__any_sync(FULL, q.ml > 0 && (dist > window || dist > q.wpos))) q.err = GMP_STATUS_BAD_OFFSET;
+      else if ((uint64_t)G0h + q.gtot > out_bytes || (uint64_t)litposh + q.glits > n_lit)
+        q.err = GMP_STATUS_OUTPUT_OVERRUN;
+      if (q.err) allow = false;
+    }
     if (allow && vec_ok && q.gtot <= GROUP_FAST_MAX) {
       // far part of the source: below the ring's reach, already in device memory
       const uint32_t rlo = max(ring_valid_lo, G0h > NEAR ? G0h - NEAR : 0u);
@@ -735,7 +792,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       const uint32_t l0 = base & ~15u, l1 = (base + q.glits + 15u) & ~15u;
       if (jc == q.jnext && l1 - l0 <= (uint32_t)LIT_STAGE) {
         const uint32_t c = l0 + 16u * lane;
-        if (c < l1) cp_async16(SB.lit[stage] + (c - l0), shadow + c);
+        if (c < l1) cp_async16(SB.lit[stage] + (c - l0), lits + c);
         q.lit_lo = l0;
         q.lit_staged = true;
       }
@@ -744,10 +801,15 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     return q;
   };
 
-  uint2 r_next = (lane < n_seq) ? rec[lane] : make_uint2(0, 0);
+  uint2 r_next = load_rec(lane);
   Prep cur = prep(0, r_next, 0, 0, 0, true, 0);
-  r_next = (32 + lane < n_seq) ? rec[32 + lane] : make_uint2(0, 0);
+  r_next = load_rec(32 + lane);
   for (uint32_t g = 0; g < n_groups_total; g++) {
+    if (cur.err) {
+      cp_async_wait_all();
+      if (lane == 0) set_status(status, cur.err);
+      return;
+    }
     const int stage = (int)(g & 1u);
     const bool fast = cur.gtot <= GROUP_FAST_MAX;
     // prepare group g+1 (staging only if this group leaves the ring's reach unchanged)
@@ -755,10 +817,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     Prep nxt = prep(g + 1, r_next, G0 + cur.gtot, litpos + cur.glits, cur.jnext, fast, stage ^ 1);
     GMP_TSTAMP(tg1);
     GMP_TADD(0, tg0, tg1);
-    {
-      const uint32_t t2 = (g + 2) * 32 + lane;
-      r_next = t2 < n_seq ? rec[t2] : make_uint2(0, 0);
-    }
+    r_next = load_rec((g + 2) * 32 + lane);
     cp_async_wait_1();  // this group's staging has landed
     __syncwarp();
     GMP_TSTAMP(tg2);
@@ -774,7 +833,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
           const uint8_t* ls = SB.lit[stage] + (lsrc - cur.lit_lo);
           for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = ls[i];
         } else {
-          for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = shadow[lsrc + i];
+          for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = lits[lsrc + i];
         }
       }
       __syncwarp();
@@ -832,7 +891,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       // a group too large for the ring: write it straight to device memory
       for (uint32_t c = flushed + lane; c < G0; c += 32u) out_blk[c] = ring[c & RING_MASK];
       __syncwarp();
-      for (uint32_t i = 0; i < ll; i++) out_blk[dst + i] = shadow[lsrc + i];
+      for (uint32_t i = 0; i < ll; i++) out_blk[dst + i] = lits[lsrc + i];
       __syncwarp();
       if (de && de_group_ok(rpos, wpos, ml)) {
         if (pending) copy_match_global(out_blk, rpos, wpos, ml);
@@ -862,7 +921,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   __syncwarp();
   // tail bytes not yet flushed
   for (uint32_t c = flushed + lane; c < out_bytes; c += 32u) out_blk[c] = ring[c & RING_MASK];
-  if (G0 != out_bytes && lane == 0) set_status(status, GMP_STATUS_OUTPUT_OVERRUN);
+  if ((G0 != out_bytes || (byte_fmt && litpos != n_lit)) && lane == 0) set_status(status, GMP_STATUS_OUTPUT_OVERRUN);
   __syncwarp();
   const long long t_end = clock64();
   st_acc[0] += n_groups;

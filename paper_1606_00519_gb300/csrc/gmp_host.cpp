@@ -97,9 +97,12 @@ int gmp_stream_info_parse(const void* host_stream, size_t bytes, gmp_stream_info
   I.n_blocks = rd64(s + 32);
   I.stream_bytes = rd64(s + 40);
   if (I.version != GMP_VERSION) return GMP_ERR_UNSUPPORTED;
-  if (!(I.flags & 2u)) return GMP_ERR_UNSUPPORTED;  // byte-level streams are not decoded by this build
-  if (I.block_size == 0 || I.n_sub == 0 || I.n_sub > gmp::kMaxSub || I.cwl == 0 || I.cwl > 12 || I.window == 0 ||
-      I.window > 32768 || I.min_match != 3 || I.max_match < 3 || I.max_match > 64)
+  if (I.flags & ~3u) return GMP_ERR_UNSUPPORTED;
+  const bool huffman = (I.flags & 2u) != 0;  // else byte-level blocks: no trees, no sub-blocks
+  if (huffman ? (I.n_sub == 0 || I.n_sub > gmp::kMaxSub || I.cwl == 0 || I.cwl > 12) : (I.n_sub != 0 || I.cwl != 0))
+    return GMP_ERR_FORMAT;
+  if (I.block_size == 0 || I.window == 0 || I.window > 32768 || I.min_match != 3 || I.max_match < 3 ||
+      I.max_match > 64)
     return GMP_ERR_FORMAT;
   if (I.n_blocks != (I.orig_size + I.block_size - 1) / I.block_size) return GMP_ERR_FORMAT;
   if (I.stream_bytes > bytes || I.stream_bytes < gmp::kHeaderBytes + 8 * I.n_blocks) return GMP_ERR_FORMAT;
@@ -120,7 +123,7 @@ int gmp_index_build(const void* host_stream, size_t bytes, gmp_block_ref* out, s
   }
   const uint8_t* s = static_cast<const uint8_t*>(host_stream);
   const uint64_t table_end = gmp::kHeaderBytes + 8 * I.n_blocks;
-  const uint64_t blk_hdr = (gmp::kBlockFixed + 12ull * I.n_sub + 15) & ~15ull;
+  const uint64_t blk_hdr = (I.flags & 2u) ? (gmp::kBlockFixed + 12ull * I.n_sub + 15) & ~15ull : 16ull;
   uint32_t max_out = 0, max_seq = 0;
   for (uint64_t b = 0; b < I.n_blocks; b++) {
     uint64_t off = rd64(s + gmp::kHeaderBytes + 8 * b);
