@@ -455,6 +455,128 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_batch(ctx, table, n_files, status, stream, reps):
+    """Mean ms of one batched launch over `reps` launches (CUDA events)."""
+    import torch
+    for _ in range(2):
+        ctx.decompress_batch(table, n_files, status, stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        ctx.decompress_batch(table, n_files, status, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _round_profile(gmp, table, n_files, status, stream, block_size, resolve):
+    """Rounds per group, largest round count and mean bytes resolved per
+    group in each round (rounds past 7 together) of one statistics launch."""
+    import torch
+    c = gmp.Context(max_block_out=block_size, collect_stats=True, resolve=resolve, max_files=max(n_files, 1))
+    c.stats_reset(stream)
+    c.decompress_batch(table, n_files, status, stream)
+    torch.cuda.synchronize()
+    st = c.stats()
+    c.close()
+    per_round = [round(b / g, 1) if g else 0.0 for b, g in zip(st["round_bytes"], st["round_groups"])]
+    return {"rounds_per_group": round(st["rounds"] / max(st["groups"], 1), 3), "max_rounds": st["max_rounds"],
+            "bytes_per_group_in_round": per_round}
+
+
+def run_sweep(args):
+    """Ablation of the LZ77 resolution strategies (Sec. 5.2): Sequential
+    Copying (SC), Multi-Round Resolution (MRR) and Dependency Elimination
+    (DE) on the text and CSV workloads in both stream formats, then MRR and SC
+    against the back-reference nesting depth (1..32 dependent copies per
+    32-sequence group; the nesting-depth data sets of Sec. 5.2, one 256 KiB
+    block per file, as many files as --sweep-bytes holds).  Every decoded
+    output is compared with the input before it is timed."""
+    import torch
+    import paper_1606_00519_gb300 as gmp
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    reps = max(3, args.steps)
+    strategies = []
+    for wl in ("text256m", "csv1g"):
+        w = datagen.WORKLOADS[wl]
+        data = w.data(min(w.size, args.sweep_bytes))
+        ref = torch.from_numpy(data).cuda()
+        for fmt in ("bit", "byte"):
+            for mode in ("mrr", "de"):
+                st = gmp.compress(data, w.block_size, w.n_sub, w.window, de=(mode == "de"), byte_mode=(fmt == "byte"))
+                ds = gmp.DeviceStream(st)
+                out = torch.empty(data.size, dtype=torch.uint8, device="cuda")
+                table = gmp.make_file_table([ds.file_desc(out)])
+                status = torch.zeros(1, dtype=torch.int32, device="cuda")
+                for resolve in (("sc", "mrr", "auto") if mode == "de" else ("sc", "mrr")):
+                    ctx = gmp.Context(max_block_out=w.block_size, resolve=resolve)
+                    out.zero_()
+                    ctx.decompress_batch(table, 1, status, stream)
+                    torch.cuda.synchronize()
+                    if int(status.item()) != 0 or not torch.equal(out, ref):
+                        raise SystemExit(f"sweep: {wl} {fmt} {mode} {resolve} is not byte-exact")
+                    ms = _time_batch(ctx, table, 1, status, stream, reps)
+                    ctx.close()
+                    name = {"sc": "SC", "mrr": "MRR", "auto": "DE"}[resolve]
+                    row = {"workload": wl, "bytes": int(data.size), "format": fmt, "stream": mode,
+                           "strategy": name, "ms": round(ms, 3), "gbs": round(data.size / ms / 1e6, 2),
+                           "ratio": round(data.size / st.size, 4)}
+                    row.update(_round_profile(gmp, table, 1, status, stream, w.block_size, resolve))
+                    strategies.append(row)
+                    print(json.dumps(row), file=sys.stderr, flush=True)
+                del ds, out, table
+        del ref
+    nesting = []
+    # one block of at most 256 KiB per file: n_inst 17-byte instances after
+    # m initial strings
+    n_inst = ((256 * KiB - 17 * 33) // 17) // 32 * 32
+    for m in (1, 2, 4, 8, 16, 32):
+        for fmt in ("bit", "byte"):
+            files, total = [], 0
+            while total < args.sweep_bytes:
+                ts = datagen.nesting_tokens(seed=1000 * m + len(files), m=m, n_inst=n_inst)
+                st = gmp.encode_tokens(ts.lit_len, ts.mlen, ts.off, ts.lits, block_size=256 * KiB, n_sub=32,
+                                       byte_mode=(fmt == "byte"))
+                ds = gmp.DeviceStream(st)
+                out = torch.empty(max(ds.orig_size, 16), dtype=torch.uint8, device="cuda")
+                files.append((ds, out))
+                total += ds.orig_size
+            table = gmp.make_file_table([ds.file_desc(out, ds.orig_size) for ds, out in files])
+            status = torch.zeros(len(files), dtype=torch.int32, device="cuda")
+            first = None
+            for resolve in ("mrr", "sc"):
+                ctx = gmp.Context(max_block_out=256 * KiB, resolve=resolve, max_files=len(files))
+                ctx.decompress_batch(table, len(files), status, stream)
+                torch.cuda.synchronize()
+                if int(status.abs().sum().item()) != 0:
+                    raise SystemExit(f"sweep: nesting m={m} {fmt} {resolve} reported an error")
+                # both strategies must give the same bytes (the GPU tests
+                # compare these streams with the serial LZ77 decode)
+                got = torch.cat([out[:ds.orig_size] for ds, out in files])
+                if first is None:
+                    first = got.clone()
+                elif not torch.equal(got, first):
+                    raise SystemExit(f"sweep: nesting m={m} {fmt}: strategies disagree")
+                ms = _time_batch(ctx, table, len(files), status, stream, reps)
+                ctx.close()
+                row = {"depth": 32 // m, "strings": m, "format": fmt, "strategy": resolve.upper(),
+                       "files": len(files), "bytes": total, "ms": round(ms, 3), "gbs": round(total / ms / 1e6, 2)}
+                row.update(_round_profile(gmp, table, len(files), status, stream, 256 * KiB, resolve))
+                nesting.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+            del files, table, first
+    line = {"metric": "LZ77 resolution strategies: decompressed GB/s", "unit": "GB/s", "n_gpus": 1,
+            "steps": reps, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "strategy ablation on text256m and csv1g (first "
+                                   f"{args.sweep_bytes // MiB} MiB), nesting-depth sets of {args.sweep_bytes // MiB} MiB",
+                       "launch": "one batched launch per measurement; single-stream launches for the strategies"},
+            "strategies": strategies, "nesting": nesting}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving: Poisson arrivals of requests (16 KiB..64 MiB, mixed content
     and modes) admitted under a device-memory budget by the continuous-batching
@@ -569,6 +691,8 @@ def main():
     ap.add_argument("--batch-files", type=int, default=4096)
     ap.add_argument("--batch-cap", type=int, default=GiB, help="seeded prefix of the file list up to this many bytes "
                                                                  "(0: all files)")
+    ap.add_argument("--sweep", action="store_true", help="resolution strategies and nesting-depth sweep")
+    ap.add_argument("--sweep-bytes", type=int, default=256 * MiB)
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the decode step")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-pool", type=int, default=96)
@@ -577,7 +701,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.batch:
+    if args.sweep:
+        run_sweep(args)
+    elif args.batch:
         run_batch(args)
     elif args.serve:
         run_serve(args)

@@ -172,6 +172,23 @@ size_t gmp_compress_bound(size_t n, const gmp_compress_opts* o);
 int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* o, void* host_out, size_t cap,
                  size_t* out_bytes);
 
+/* One-block stream holding a given LZ77 parse (the entropy-coding half of
+   the compressor, for callers with their own match finder, and for streams
+   with a chosen dependency structure such as the nesting-depth data sets of
+   Sec. 5.2).  Sequence i is lit_len[i] literal bytes, taken in order from
+   lits (n_lits bytes in all), then a back-reference of match_len[i] bytes
+   (0 = none) at distance dist[i].  Host arrays.  Checks: match lengths 3 ..
+   o->max_match, distances 1 .. min(o->window, bytes before the copy), total
+   output <= o->block_size, the literals used exactly; for Huffman blocks only
+   the last sequence may lack a back-reference (Byte blocks cut literal
+   strings over 1023 bytes).  The DE flag (o->de) is written as given and not
+   verified; the decoder checks it per group.  GMP_ERR_INVALID_ARG on a bad
+   parse, GMP_ERR_CAPACITY if cap is too small (2 * n_lits + 5 * n_seq +
+   1280 bytes always suffice). */
+int gmp_encode_tokens(const uint32_t* lit_len, const uint32_t* match_len, const uint32_t* dist, size_t n_seq,
+                      const uint8_t* lits, size_t n_lits, const gmp_compress_opts* o, void* host_out, size_t cap,
+                      size_t* out_bytes);
+
 /* ------------------------------------------------------------------------ */
 /* Decoder context. */
 
@@ -183,7 +200,16 @@ typedef struct {
   uint32_t ctas_per_sm;     /* 0 = as many as fit */
   uint32_t collect_stats;   /* 1: count groups and MRR rounds (small cost) */
   uint32_t max_files;       /* largest n_files of gmp_decompress_batch (default 65536) */
+  uint32_t resolve;         /* back-reference resolution, a gmp_resolve (default GMP_RESOLVE_AUTO) */
 } gmp_context_opts;
+
+/* How a context resolves each 32-sequence group's back-references.  AUTO:
+   streams with the DE flag in one pass (groups that break the DE property by
+   MRR), others by Multi-Round Resolution (Fig. 5, Sec. 4.1).  MRR: MRR even
+   for DE streams.  SC: Sequential Copying, one back-reference at a time in
+   sequence order, the paper's baseline (Sec. 5.2).  All give the same bytes;
+   MRR and SC exist to measure the strategies against each other. */
+typedef enum { GMP_RESOLVE_AUTO = 0, GMP_RESOLVE_MRR = 1, GMP_RESOLVE_SC = 2 } gmp_resolve;
 
 void gmp_context_opts_default(gmp_context_opts* o);
 /* Creates a context on `device`: allocates the scratch of one persistent
@@ -257,15 +283,19 @@ int gmp_autotune(gmp_context* ctx, const gmp_file_desc* d_files, size_t n_files,
 
 /* ------------------------------------------------------------------------ */
 /* Statistics of the launches since gmp_stats_reset (collect_stats=1):
-   32-sequence groups resolved, MRR rounds, groups of a DE stream that broke
-   the DE property and were resolved by MRR, blocks decoded, the largest
+   32-sequence groups resolved, resolution rounds, groups of a DE stream that
+   broke the DE property and were resolved by MRR, blocks decoded, the largest
    round count of a group, and SM clock cycles summed over warps spent on
    block setup (headers and lookup tables), Huffman decoding and LZ77
-   resolution. */
+   resolution.  Per round r (rounds after the 8th in bin 7): back-reference
+   bytes copied in round r and groups that ran a round r, so that
+   round_bytes[r] / round_groups[r] is the mean bytes resolved per group in
+   round r (the quantity of the paper's bytes-per-round measurement, Sec. 5.2). */
 typedef struct {
   uint64_t groups, rounds, de_fallback_groups, blocks, max_rounds;
   uint64_t cycles_tables, cycles_huffman, cycles_lz77;
   uint64_t detail[8]; /* stage timers of profiling builds (GMP_PHASE_TIMERS), else 0 */
+  uint64_t round_bytes[8], round_groups[8];
 } gmp_stats;
 int gmp_stats_reset(gmp_context* ctx, void* stream);
 int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device */

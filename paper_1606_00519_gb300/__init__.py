@@ -25,6 +25,7 @@ from ._native import (BlockRef, Completion, CompressOpts, ContextOpts, FileDesc,
                       Tuning)
 
 OK = 0
+RESOLVE = {"auto": 0, "mrr": 1, "sc": 2}
 STATUS_NAMES = {0: "OK", 1: "BAD_HEADER", 2: "CORRUPT_SYMBOL", 3: "BITSTREAM", 4: "BAD_OFFSET",
                 5: "OUTPUT_OVERRUN", 6: "MRR_NO_PROGRESS", 7: "CAPACITY"}
 ERROR_NAMES = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "CUDA", -4: "UNSUPPORTED", -5: "FORMAT", -6: "NOMEM"}
@@ -87,6 +88,29 @@ def compress(data, block_size: int = 256 << 10, n_sub: int = 32, window: int = 3
     return out[:n.value]
 
 
+def encode_tokens(lit_len, match_len, dist, lits, block_size: int | None = None, n_sub: int = 32,
+                  window: int = 32768, cwl: int = 12, max_match: int = 64, de: bool = False,
+                  byte_mode: bool = False) -> np.ndarray:
+    """One-block stream of the given LZ77 parse (sequence i: lit_len[i]
+    literals from lits, then match_len[i] bytes at distance dist[i]).
+    block_size defaults to the parse's output size."""
+    L = _native.lib()
+    ll = np.ascontiguousarray(lit_len, np.uint32)
+    ml = np.ascontiguousarray(match_len, np.uint32)
+    di = np.ascontiguousarray(dist, np.uint32)
+    lt = _np_bytes(lits)
+    total = int(ll.sum(dtype=np.int64) + ml.sum(dtype=np.int64))
+    o = CompressOpts(block_size or max(total, 1), n_sub, window, cwl, max_match, 64, 1 if de else 0, 0, 1,
+                     1 if byte_mode else 0)
+    cap = 2 * lt.size + 5 * ll.size + 1280
+    out = np.empty(cap, np.uint8)
+    n = ctypes.c_size_t()
+    _check(L.gmp_encode_tokens(_ptr(ll) if ll.size else None, _ptr(ml) if ml.size else None,
+                               _ptr(di) if di.size else None, ll.size, _ptr(lt) if lt.size else None, lt.size,
+                               ctypes.byref(o), _ptr(out), cap, ctypes.byref(n)), "gmp_encode_tokens")
+    return out[:n.value]
+
+
 def stream_info(stream) -> StreamInfo:
     s = _np_bytes(stream)
     info = StreamInfo()
@@ -140,13 +164,16 @@ class Context:
     """A decoder context (scratch for one persistent launch) on one device."""
 
     def __init__(self, device: int | None = None, max_block_out: int = 256 << 10, warps_per_cta: int = 0,
-                 ctas_per_sm: int = 0, collect_stats: bool = False, max_files: int = 65536):
+                 ctas_per_sm: int = 0, collect_stats: bool = False, max_files: int = 65536, resolve: str = "auto"):
+        """resolve: "auto" (DE streams in one pass, others by MRR), "mrr" (MRR
+        always) or "sc" (sequential copying, the paper's baseline)."""
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the decoder runs only on the GPU")
         self.device = torch.cuda.current_device() if device is None else int(device)
         self._L = _native.lib()
-        o = ContextOpts(max_block_out, warps_per_cta, ctas_per_sm, 1 if collect_stats else 0, max_files)
+        o = ContextOpts(max_block_out, warps_per_cta, ctas_per_sm, 1 if collect_stats else 0, max_files,
+                        RESOLVE[resolve])
         h = ctypes.c_void_p()
         _check(self._L.gmp_context_create(ctypes.byref(h), self.device, ctypes.byref(o)), "gmp_context_create")
         self._h = h
@@ -222,8 +249,10 @@ class Context:
     def stats(self) -> dict:
         s = Stats()
         _check(self._L.gmp_stats_read(self._h, ctypes.byref(s)), "gmp_stats_read")
-        d = {k: int(getattr(s, k)) for k, _ in Stats._fields_ if k != "detail"}
-        d["detail"] = [int(x) for x in s.detail]
+        arrays = ("detail", "round_bytes", "round_groups")
+        d = {k: int(getattr(s, k)) for k, _ in Stats._fields_ if k not in arrays}
+        for k in arrays:
+            d[k] = [int(x) for x in getattr(s, k)]
         return d
 
     def decompress_host(self, stream, out: np.ndarray | None = None, cuda_stream=None):

@@ -100,7 +100,7 @@ class CompressOpts(ctypes.Structure):
 class ContextOpts(ctypes.Structure):
     _fields_ = [("max_block_out", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("collect_stats", ctypes.c_uint32),
-                ("max_files", ctypes.c_uint32)]
+                ("max_files", ctypes.c_uint32), ("resolve", ctypes.c_uint32)]
 
 
 class FileDesc(ctypes.Structure):
@@ -128,7 +128,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("de_fallback_groups", ctypes.c_uint64),
                 ("blocks", ctypes.c_uint64), ("max_rounds", ctypes.c_uint64),
                 ("cycles_tables", ctypes.c_uint64), ("cycles_huffman", ctypes.c_uint64),
-                ("cycles_lz77", ctypes.c_uint64), ("detail", ctypes.c_uint64 * 8)]
+                ("cycles_lz77", ctypes.c_uint64), ("detail", ctypes.c_uint64 * 8),
+                ("round_bytes", ctypes.c_uint64 * 8), ("round_groups", ctypes.c_uint64 * 8)]
 
 
 def _declare(L):
@@ -141,6 +142,7 @@ def _declare(L):
     L.gmp_compress_bound.argtypes = [sz, P(CompressOpts)]
     L.gmp_compress_bound.restype = sz
     L.gmp_compress.argtypes = [vp, sz, P(CompressOpts), vp, sz, P(sz)]
+    L.gmp_encode_tokens.argtypes = [vp, vp, vp, sz, vp, sz, P(CompressOpts), vp, sz, P(sz)]
     L.gmp_context_opts_default.argtypes = [P(ContextOpts)]
     L.gmp_context_opts_default.restype = None
     L.gmp_context_create.argtypes = [P(vp), i32, P(ContextOpts)]

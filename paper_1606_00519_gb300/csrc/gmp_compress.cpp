@@ -367,6 +367,46 @@ void encode_block_byte(const uint8_t* in, uint32_t n, const std::vector<Seq>& se
   }
 }
 
+// File header, block offset table, blocks and tail padding (gmp.h).
+int assemble(const gmp_compress_opts& o, size_t n, const std::vector<std::vector<uint8_t>>& blocks, void* host_out,
+             size_t cap, size_t* out_bytes) {
+  const size_t nb = blocks.size();
+  uint64_t pos = (gmp::kHeaderBytes + 8 * nb + 15) & ~uint64_t(15);
+  uint64_t total = pos;
+  for (auto& b : blocks) total += b.size();
+  total += 16;
+  if (total > cap) return GMP_ERR_CAPACITY;
+  uint8_t* out = static_cast<uint8_t*>(host_out);
+  memset(out, 0, pos);
+  memcpy(out, "GMP1", 4);
+  put_le(out + 4, GMP_VERSION, 2);
+  put_le(out + 6, (o.de ? 1u : 0u) | (o.byte_mode ? 0u : 2u), 2);
+  put_le(out + 8, o.block_size, 4);
+  put_le(out + 12, o.byte_mode ? 0u : o.n_sub, 2);
+  out[14] = (uint8_t)(o.byte_mode ? 0u : o.cwl);
+  put_le(out + 16, o.window, 4);
+  out[20] = 3;
+  out[21] = (uint8_t)o.max_match;
+  put_le(out + 24, n, 8);
+  put_le(out + 32, nb, 8);
+  put_le(out + 40, total, 8);
+  for (size_t b = 0; b < nb; b++) {
+    put_le(out + gmp::kHeaderBytes + 8 * b, pos, 8);
+    memcpy(out + pos, blocks[b].data(), blocks[b].size());
+    pos += blocks[b].size();
+  }
+  memset(out + pos, 0, 16);
+  *out_bytes = total;
+  return GMP_OK;
+}
+
+bool opts_ok(const gmp_compress_opts& o) {
+  if (o.block_size == 0 || o.window == 0 || o.window > 32768 || o.max_match < 3 || o.max_match > 64 ||
+      o.chain_depth == 0 || o.byte_mode > 1)
+    return false;
+  return o.byte_mode || (o.n_sub >= 1 && o.n_sub <= gmp::kMaxSub && o.cwl >= 9 && o.cwl <= 12);
+}
+
 }  // namespace
 
 extern "C" {
@@ -397,10 +437,7 @@ int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* opts, v
                  size_t* out_bytes) {
   if ((!host_in && n) || !opts || !host_out || !out_bytes) return GMP_ERR_INVALID_ARG;
   gmp_compress_opts o = *opts;
-  if (o.block_size == 0 || o.window == 0 || o.window > 32768 || o.max_match < 3 || o.max_match > 64 ||
-      o.chain_depth == 0 || o.byte_mode > 1)
-    return GMP_ERR_INVALID_ARG;
-  if (!o.byte_mode && (o.n_sub == 0 || o.n_sub > gmp::kMaxSub || o.cwl < 9 || o.cwl > 12)) return GMP_ERR_INVALID_ARG;
+  if (!opts_ok(o)) return GMP_ERR_INVALID_ARG;
   const uint8_t* in = static_cast<const uint8_t*>(host_in);
   const size_t nb = (n + o.block_size - 1) / o.block_size;
   std::vector<std::vector<uint8_t>> blocks;
@@ -435,33 +472,43 @@ int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* opts, v
   worker();
   for (auto& t : th) t.join();
   if (failed) return GMP_ERR_NOMEM;
-  uint64_t pos = (gmp::kHeaderBytes + 8 * nb + 15) & ~uint64_t(15);
-  uint64_t total = pos;
-  for (auto& b : blocks) total += b.size();
-  total += 16;
-  if (total > cap) return GMP_ERR_CAPACITY;
-  uint8_t* out = static_cast<uint8_t*>(host_out);
-  memset(out, 0, pos);
-  memcpy(out, "GMP1", 4);
-  put_le(out + 4, GMP_VERSION, 2);
-  put_le(out + 6, (o.de ? 1u : 0u) | (o.byte_mode ? 0u : 2u), 2);
-  put_le(out + 8, o.block_size, 4);
-  put_le(out + 12, o.byte_mode ? 0u : o.n_sub, 2);
-  out[14] = (uint8_t)(o.byte_mode ? 0u : o.cwl);
-  put_le(out + 16, o.window, 4);
-  out[20] = 3;
-  out[21] = (uint8_t)o.max_match;
-  put_le(out + 24, n, 8);
-  put_le(out + 32, nb, 8);
-  put_le(out + 40, total, 8);
-  for (size_t b = 0; b < nb; b++) {
-    put_le(out + gmp::kHeaderBytes + 8 * b, pos, 8);
-    memcpy(out + pos, blocks[b].data(), blocks[b].size());
-    pos += blocks[b].size();
+  return assemble(o, n, blocks, host_out, cap, out_bytes);
+}
+
+int gmp_encode_tokens(const uint32_t* lit_len, const uint32_t* match_len, const uint32_t* dist, size_t n_seq,
+                      const uint8_t* lits, size_t n_lits, const gmp_compress_opts* opts, void* host_out, size_t cap,
+                      size_t* out_bytes) {
+  if (!opts || !host_out || !out_bytes || (n_seq && (!lit_len || !match_len || !dist)) || (n_lits && !lits))
+    return GMP_ERR_INVALID_ARG;
+  const gmp_compress_opts& o = *opts;
+  if (!opts_ok(o)) return GMP_ERR_INVALID_ARG;
+  std::vector<Seq> seqs;
+  std::vector<std::vector<uint8_t>> blocks(1);
+  uint64_t pos = 0, lp = 0;
+  try {
+    seqs.reserve(n_seq);
+    for (size_t i = 0; i < n_seq; i++) {
+      const uint32_t ll = lit_len[i], ml = match_len[i], d = dist[i];
+      if (lp + ll > n_lits) return GMP_ERR_INVALID_ARG;
+      if (ml && (ml < 3 || ml > o.max_match || d == 0 || d > o.window || d > pos + ll)) return GMP_ERR_INVALID_ARG;
+      // Huffman blocks end a sequence without a back-reference only at the end of the block
+      if (!ml && !o.byte_mode && i + 1 != n_seq) return GMP_ERR_INVALID_ARG;
+      uint32_t start = (uint32_t)lp, rest = ll;
+      for (; o.byte_mode && rest > kByteMaxLit; rest -= kByteMaxLit, start += kByteMaxLit)
+        seqs.push_back(Seq{start, kByteMaxLit, 0, 0});
+      seqs.push_back(Seq{start, rest, ml, ml ? d : 0});
+      lp += ll;
+      pos += (uint64_t)ll + ml;
+      if (pos > o.block_size) return GMP_ERR_INVALID_ARG;
+    }
+    if (lp != n_lits) return GMP_ERR_INVALID_ARG;
+    if (o.byte_mode) encode_block_byte(lits, (uint32_t)pos, seqs, blocks[0]);
+    else encode_block(lits, (uint32_t)pos, seqs, o, blocks[0]);
+  } catch (...) {
+    return GMP_ERR_NOMEM;
   }
-  memset(out + pos, 0, 16);
-  *out_bytes = total;
-  return GMP_OK;
+  if (pos == 0) blocks.clear();  // an empty stream has no blocks
+  return assemble(o, pos, blocks, host_out, cap, out_bytes);
 }
 
 }  // extern "C"

@@ -29,8 +29,9 @@
 //  with each group's records checked before it is staged or copied.
 //
 // MRR reading (the printed algorithm is ambiguous, see the comment at
-// resolve_mrr_global): HWM = write position of the lowest pending lane; a lane may
-// copy once min(read_pos + length, write_pos) <= HWM.
+// resolve_group): HWM = write position of the lowest pending lane; a lane may
+// copy once min(read_pos + length, write_pos) <= HWM.  For ablation a context
+// can force MRR on DE streams or resolve by Sequential Copying (Sec. 5.2).
 //
 // Every read of the compressed stream is bounds-checked; every loop over
 // input data is bounded by sizes checked against the block header; corrupt
@@ -108,6 +109,7 @@ struct __align__(16) WarpSmem {
   uint32_t run[16];              // LUT build: running rank per length
   uint16_t sorted[N_LL + 1];
   uint8_t lens[N_LL + N_OFF + 3];
+  unsigned long long rstat[16];  // statistics: bytes copied in round r (0..7, 7 = later), groups reaching round r
 };
 static_assert(sizeof(PhaseBSmem) <= (LUT_SIZE + OFF_SIZE) * sizeof(uint16_t), "phase B fits in the LUT space");
 
@@ -124,6 +126,7 @@ struct KParams {
   uint32_t max_seq, max_out;
   unsigned long long* stats;  // [groups, rounds, de_fallback, blocks, max_rounds, cycles x3]
   int collect_stats;
+  int resolve;  // 0: by the stream's DE flag, 1: MRR always, 2: sequential copying (SC)
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -251,30 +254,59 @@ __device__ __forceinline__ void copy_match_global(uint8_t* out_blk, uint32_t rpo
   for (uint32_t i = 0; i < ml; i++) out_blk[wpos + i] = out_blk[rpos + i];
 }
 
-// Multi-Round Resolution (Fig. 5, Sec. 4.1).  The figure names the last
-// writer with count_leading_zero_bits(ballot) and waits for read_pos + length
-// <= HWM; the first picks the highest pending lane rather than the last
-// completed one, and the second never admits an overlapping copy (offset <
-// length), whose source extends into its own output.  Reading used here: the
-// lowest pending lane f = ffs(ballot(pending)) - 1 has every earlier lane
-// complete and its own literals written, so HWM = write_pos(f); a pending lane
-// copies once min(read_pos + length, write_pos) <= HWM.  Lane f always
-// qualifies, so every round resolves at least one lane and a group needs at
-// most 32 rounds; a group whose back-references do not depend on each other
-// resolves in one round.  Returns the number of rounds, or -1 on no progress.
-__device__ int resolve_mrr_global(uint8_t* out_blk, uint32_t rpos, uint32_t wpos, uint32_t ml, bool pending) {
+// Resolution of one group's back-references (Sec. 3.2.2 step (c)); `copy`
+// performs the calling lane's copy.  Strategies:
+//  RES_ONE_PASS: every back-reference at once (Dependency Elimination, Fig. 7,
+//    Sec. 4.2), for a group whose sources avoid the group's other copies;
+//  RES_MRR: Multi-Round Resolution (Fig. 5, Sec. 4.1).  The figure names the
+//    last writer with count_leading_zero_bits(ballot) and waits for read_pos +
+//    length <= HWM; the first picks the highest pending lane rather than the
+//    last completed one, and the second never admits an overlapping copy
+//    (offset < length), whose source extends into its own output.  Reading
+//    used here: the lowest pending lane f = ffs(ballot(pending)) - 1 has every
+//    earlier lane complete and its own literals written, so HWM =
+//    write_pos(f); a pending lane copies once min(read_pos + length,
+//    write_pos) <= HWM.  Lane f always qualifies, so every round resolves at
+//    least one lane and a group needs at most 32 rounds; a group whose
+//    back-references do not depend on each other resolves in one round;
+//  RES_SC: Sequential Copying, the baseline of Sec. 5.2: one back-reference
+//    per round, in sequence order.
+// Returns the number of rounds, or -1 if a round made no progress.  rstat
+// (statistics only, else null): bytes copied in round r and groups reaching
+// round r, rounds past 7 counted in bin 7.
+enum { RES_ONE_PASS = 0, RES_MRR = 1, RES_SC = 2 };
+
+// Statistics of one round: the warp's copied bytes (bytes_lane per lane).
+__device__ __forceinline__ void note_round(unsigned long long* rstat, int round, uint32_t bytes_lane) {
+  const uint32_t b = __reduce_add_sync(FULL, bytes_lane);
+  if (lane_id() == 0 && b) {
+    rstat[min(round, 7)] += b;
+    rstat[8 + min(round, 7)] += 1;
+  }
+}
+
+template <class Copy>
+__device__ __forceinline__ int resolve_group(int how, bool pending, uint32_t rpos, uint32_t wpos, uint32_t ml,
+                                             Copy&& copy, unsigned long long* rstat) {
+  const uint32_t lane = lane_id();
   int rounds = 0;
   for (;;) {
-    uint32_t votes = __ballot_sync(FULL, pending);
+    const uint32_t votes = __ballot_sync(FULL, pending);
     if (votes == 0) break;
     if (rounds == 32) return -1;
-    int f = __ffs(votes) - 1;
-    uint32_t hwm = __shfl_sync(FULL, wpos, f);
-    uint32_t lim = min(rpos + ml, wpos);
-    if (pending && lim <= hwm) {
-      copy_match_global(out_blk, rpos, wpos, ml);
+    const int f = __ffs(votes) - 1;
+    bool go = pending;
+    if (how == RES_SC) {
+      go = (int)lane == f;
+    } else if (how == RES_MRR) {
+      const uint32_t hwm = __shfl_sync(FULL, wpos, f);
+      go = pending && min(rpos + ml, wpos) <= hwm;
+    }
+    if (go) {
+      copy();
       pending = false;
     }
+    if (rstat) note_round(rstat, rounds, go ? ml : 0u);
     __syncwarp();
     rounds++;
   }
@@ -375,6 +407,18 @@ __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v
   for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
 }
 
+// Out-of-line resolutions, kept out of the decode loop's code: Sequential
+// Copying of a ring-resident group (ablation only), and every strategy for a
+// group written straight to device memory (groups too large for the ring).
+__device__ __noinline__ int resolve_sc_ring(uint8_t* ring, SrcView sv, uint32_t rpos, uint32_t wpos, uint32_t ml,
+                                            bool pending, unsigned long long* rstat) {
+  return resolve_group(RES_SC, pending, rpos, wpos, ml, [&] { copy_match_words(ring, sv, rpos, wpos, ml); }, rstat);
+}
+__device__ __noinline__ int resolve_global(int how, uint8_t* out_blk, uint32_t rpos, uint32_t wpos, uint32_t ml,
+                                           bool pending, unsigned long long* rstat) {
+  return resolve_group(how, pending, rpos, wpos, ml, [&] { copy_match_global(out_blk, rpos, wpos, ml); }, rstat);
+}
+
 // DE property check of one group (Sec. 4.2): each back-reference's source
 // bytes before its own write position must avoid every other back-reference
 // of the group.  Write positions rise with the lane, so the only candidate to
@@ -396,11 +440,12 @@ __device__ __forceinline__ bool de_group_ok(uint32_t rpos, uint32_t wpos, uint32
 
 // ---------------------------------------------------------------------------
 // Decode one block.  Returns false if an error was recorded.
+template <bool STATS>
 __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc& F, uint64_t b, int32_t* status,
                              uint8_t* slot, unsigned long long* st_acc) {
   const uint32_t lane = lane_id();
   const uint8_t* comp = F.comp;
-  const long long t_begin = clock64();
+  const long long t_begin = STATS ? clock64() : 0;
 #ifdef GMP_PHASE_TIMERS
   unsigned long long tdet[6] = {0, 0, 0, 0, 0, 0};
 #endif
@@ -434,7 +479,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     if ((br.comp_offset & 15) || br.comp_offset > F.comp_bytes || br.comp_bytes > F.comp_bytes - br.comp_offset ||
         br.out_offset > F.out_cap || br.out_bytes > F.out_cap - br.out_offset)
       err = GMP_STATUS_OUTPUT_OVERRUN;
-    else if (br.comp_bytes < (byte_fmt ? 16ull : 192 + 12ull * K))
+    else if (br.comp_bytes < (byte_fmt ? 16ull : (192 + 12ull * K + 15) & ~15ull))  // through the bitstream start
       err = GMP_STATUS_BAD_HEADER;
   }
   if (err) {
@@ -478,7 +523,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     }
     K = 1;
     lits = B + lit_off;
-    t_tables = t_phase_a = clock64();
+    t_tables = t_phase_a = STATS ? clock64() : 0;
     __syncwarp();
   } else {
     const uint32_t bs_off = (192u + 12u * K + 15u) & ~15u;  // bitstream start within the block
@@ -551,7 +596,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       return;
     }
 
-    t_tables = clock64();
+    t_tables = STATS ? clock64() : 0;
     // ---- Phase A: lane per sub-block Huffman decode (Sec. 3.2.1)
     // Every lane of the warp takes one symbol per step (a literal, or a length
     // followed by its offset), with the literal / back-reference work done under
@@ -691,7 +736,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       }
     }
     __syncwarp();
-    t_phase_a = clock64();
+    t_phase_a = STATS ? clock64() : 0;
   }  // Huffman blocks
 
   // ---- Phase B: 32 sequences per step (Sec. 3.2.2)
@@ -705,6 +750,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   uint8_t* ring = SB.ring;
   uint32_t G0 = 0, litpos = 0, flushed = 0, ring_valid_lo = 0;
   unsigned long long n_groups = 0, n_rounds = 0, n_fallback = 0, max_rounds = 0;
+  unsigned long long* rstat = STATS ? S.rstat : nullptr;
   const uint32_t n_groups_total = (n_seq + 31) / 32;
 
   struct Prep {
@@ -841,15 +887,18 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       GMP_TADD(2, tg2, tg3);
       const SrcView sv{ring, SB.far[stage][lane], out_blk, ring_lo, cur.far_lo, cur.far_hi};
       // DE: every source below the group start passes at once; otherwise the
-      // exact per-group check decides (de_group_ok)
-      const bool de_ok = de && (__all_sync(FULL, !pending || rpos + ml <= G0) || de_group_ok(rpos, wpos, ml));
+      // exact per-group check decides (de_group_ok); a group that fails it is
+      // resolved by MRR
+      const bool de_ok = de && P.resolve == 0 &&
+                         (__all_sync(FULL, !pending || rpos + ml <= G0) || de_group_ok(rpos, wpos, ml));
       if (de_ok) {
         if (pending) copy_match_words(ring, sv, rpos, wpos, ml);
         __syncwarp();
         rounds = __ballot_sync(FULL, pending) ? 1 : 0;
-      } else {
-        if (de) n_fallback++;
-        // Multi-Round Resolution (reading at resolve_mrr_global): HWM = write
+        if (rstat) note_round(rstat, 0, pending ? ml : 0u);
+      } else if (P.resolve != 2) {
+        if (de && P.resolve == 0) n_fallback++;
+        // Multi-Round Resolution (reading at resolve_group): HWM = write
         // position of the lowest pending lane
         bool pend = pending;
         rounds = 0;
@@ -861,13 +910,17 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
             break;
           }
           const uint32_t hwm = __shfl_sync(FULL, wpos, __ffs(votes) - 1);
-          if (pend && min(rpos + ml, wpos) <= hwm) {
+          const bool go = pend && min(rpos + ml, wpos) <= hwm;
+          if (go) {
             copy_match_words(ring, sv, rpos, wpos, ml);
             pend = false;
           }
+          if (rstat) note_round(rstat, rounds, go ? ml : 0u);
           __syncwarp();
           rounds++;
         }
+      } else {
+        rounds = resolve_sc_ring(ring, sv, rpos, wpos, ml, pending, rstat);
       }
       GMP_TSTAMP(tg4);
       GMP_TADD(3, tg3, tg4);
@@ -893,14 +946,12 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       __syncwarp();
       for (uint32_t i = 0; i < ll; i++) out_blk[dst + i] = lits[lsrc + i];
       __syncwarp();
-      if (de && de_group_ok(rpos, wpos, ml)) {
-        if (pending) copy_match_global(out_blk, rpos, wpos, ml);
-        __syncwarp();
-        rounds = __ballot_sync(FULL, pending) ? 1 : 0;
-      } else {
-        if (de) n_fallback++;
-        rounds = resolve_mrr_global(out_blk, rpos, wpos, ml, pending);
+      int how = P.resolve == 2 ? RES_SC : RES_MRR;
+      if (de && P.resolve == 0) {
+        if (de_group_ok(rpos, wpos, ml)) how = RES_ONE_PASS;
+        else n_fallback++;
       }
+      rounds = resolve_global(how, out_blk, rpos, wpos, ml, pending, rstat);
       flushed = G1;
       ring_valid_lo = G1;
     }
@@ -923,7 +974,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   for (uint32_t c = flushed + lane; c < out_bytes; c += 32u) out_blk[c] = ring[c & RING_MASK];
   if ((G0 != out_bytes || (byte_fmt && litpos != n_lit)) && lane == 0) set_status(status, GMP_STATUS_OUTPUT_OVERRUN);
   __syncwarp();
-  const long long t_end = clock64();
+  const long long t_end = STATS ? clock64() : 0;
   st_acc[0] += n_groups;
   st_acc[1] += n_rounds;
   st_acc[2] += n_fallback;
@@ -938,6 +989,9 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
 }
 
 // Persistent kernel: warps take work items until none are left.
+// STATS: the statistics build (per-block counters, clocks and round
+// histograms); the other instance carries none of that code.
+template <bool STATS>
 __global__ void __launch_bounds__(32 * 16, 1) decode_kernel(const KParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t warp = threadIdx.x >> 5;
@@ -949,6 +1003,8 @@ __global__ void __launch_bounds__(32 * 16, 1) decode_kernel(const KParams P) {
   if (P.files) total = P.item_start[P.n_files];
   else total = P.single.n_blocks;
   unsigned long long st_acc[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (lane < 16) S.rstat[lane] = 0;
+  __syncwarp();
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(P.counter, 1ull);
@@ -971,10 +1027,10 @@ __global__ void __launch_bounds__(32 * 16, 1) decode_kernel(const KParams P) {
     } else {
       F = P.single;
     }
-    decode_block(S, P, F, b, P.status + file, slot, st_acc);
+    decode_block<STATS>(S, P, F, b, P.status + file, slot, st_acc);
     __syncwarp();
   }
-  if (P.collect_stats && lane == 0 && st_acc[3]) {
+  if (STATS && lane == 0 && st_acc[3]) {
     atomicAdd(&P.stats[0], st_acc[0]);
     atomicAdd(&P.stats[1], st_acc[1]);
     atomicAdd(&P.stats[2], st_acc[2]);
@@ -986,6 +1042,10 @@ __global__ void __launch_bounds__(32 * 16, 1) decode_kernel(const KParams P) {
 #ifdef GMP_PHASE_TIMERS
     for (int i = 8; i < 14; i++) atomicAdd(&P.stats[i], st_acc[i]);
 #endif
+  }
+  if (STATS && st_acc[3]) {
+    __syncwarp();
+    if (lane < 16 && S.rstat[lane]) atomicAdd(&P.stats[16 + lane], S.rstat[lane]);
   }
 }
 
@@ -1038,18 +1098,22 @@ namespace gmp {
 size_t warp_smem_bytes() { return sizeof(WarpSmem); }
 
 cudaError_t configure_kernel(size_t smem_bytes) {
-  return cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(decode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(decode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel, warps_per_cta * 32, smem_bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false>, warps_per_cta * 32,
+                                                       smem_bytes);
 }
 
 cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, const uint64_t* item_start,
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,
                           unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,
                           uint32_t max_seq, uint32_t max_out, unsigned long long* stats, int collect_stats,
-                          cudaStream_t stream) {
+                          int resolve, cudaStream_t stream) {
   KParams P;
   P.files = files;
   P.item_start = item_start;
@@ -1065,11 +1129,13 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
   P.max_out = max_out;
   P.stats = stats;
   P.collect_stats = collect_stats;
+  P.resolve = resolve;
   // the attribute is per kernel, so set it for this launch's shape (contexts
   // with different shapes may share the process)
   cudaError_t e = configure_kernel(shape.smem_bytes);
   if (e != cudaSuccess) return e;
-  decode_kernel<<<shape.grid, shape.warps_per_cta * 32, shape.smem_bytes, stream>>>(P);
+  if (collect_stats) decode_kernel<true><<<shape.grid, shape.warps_per_cta * 32, shape.smem_bytes, stream>>>(P);
+  else decode_kernel<false><<<shape.grid, shape.warps_per_cta * 32, shape.smem_bytes, stream>>>(P);
   return cudaGetLastError();
 }
 

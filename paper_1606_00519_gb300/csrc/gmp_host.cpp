@@ -151,6 +151,7 @@ void gmp_context_opts_default(gmp_context_opts* o) {
   o->ctas_per_sm = 0;
   o->collect_stats = 0;
   o->max_files = 65536;
+  o->resolve = GMP_RESOLVE_AUTO;
 }
 
 static int context_alloc_scratch(gmp_context* c) {
@@ -192,7 +193,8 @@ int gmp_context_create(gmp_context** ctx, int device, const gmp_context_opts* op
   if (!c) return GMP_ERR_NOMEM;
   if (opts) c->opts = *opts;
   else gmp_context_opts_default(&c->opts);
-  if (c->opts.max_block_out == 0 || c->opts.max_block_out > (64u << 20) || c->opts.max_files == 0) {
+  if (c->opts.max_block_out == 0 || c->opts.max_block_out > (64u << 20) || c->opts.max_files == 0 ||
+      c->opts.resolve > GMP_RESOLVE_SC) {
     delete c;
     return GMP_ERR_INVALID_ARG;
   }
@@ -259,7 +261,8 @@ int gmp_decompress(gmp_context* c, const uint8_t* d_comp, size_t comp_bytes, con
   uint64_t ctas_needed = (warps_needed + shape.warps_per_cta - 1) / shape.warps_per_cta;
   if ((uint64_t)shape.grid > ctas_needed) shape.grid = (int)ctas_needed;
   GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, c->counter, c->scratch, c->slot_bytes,
-                              c->shadow_off, c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats, s));
+                              c->shadow_off, c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats,
+                              (int)c->opts.resolve, s));
   return GMP_OK;
 }
 
@@ -275,7 +278,7 @@ int gmp_decompress_batch(gmp_context* c, const gmp_file_desc* d_files, size_t n_
   GMP_CUDA(gmp::launch_batch_prefix(d_files, (uint32_t)n_files, c->item_start, s));
   GMP_CUDA(gmp::launch_decode(c->shape, d_files, c->item_start, (uint32_t)n_files, nullptr, d_status, c->counter,
                               c->scratch, c->slot_bytes, c->shadow_off, c->max_seq, c->max_out, c->stats,
-                              (int)c->opts.collect_stats, s));
+                              (int)c->opts.collect_stats, (int)c->opts.resolve, s));
   return GMP_OK;
 }
 
@@ -390,14 +393,14 @@ int gmp_autotune(gmp_context* c, const gmp_file_desc* d_files, size_t n_files, i
 int gmp_stats_reset(gmp_context* c, void* stream) {
   if (!c) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
-  GMP_CUDA(cudaMemsetAsync(c->stats, 0, 16 * sizeof(unsigned long long), static_cast<cudaStream_t>(stream)));
+  GMP_CUDA(cudaMemsetAsync(c->stats, 0, 32 * sizeof(unsigned long long), static_cast<cudaStream_t>(stream)));
   return GMP_OK;
 }
 
 int gmp_stats_read(gmp_context* c, gmp_stats* out) {
   if (!c || !out) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
-  unsigned long long v[16];
+  unsigned long long v[32];
   GMP_CUDA(cudaDeviceSynchronize());
   GMP_CUDA(cudaMemcpy(v, c->stats, sizeof(v), cudaMemcpyDeviceToHost));
   out->groups = v[0];
@@ -408,7 +411,11 @@ int gmp_stats_read(gmp_context* c, gmp_stats* out) {
   out->cycles_tables = v[5];
   out->cycles_huffman = v[6];
   out->cycles_lz77 = v[7];
-  for (int i = 0; i < 8; i++) out->detail[i] = v[8 + i];
+  for (int i = 0; i < 8; i++) {
+    out->detail[i] = v[8 + i];
+    out->round_bytes[i] = v[16 + i];
+    out->round_groups[i] = v[24 + i];
+  }
   return GMP_OK;
 }
 

@@ -101,7 +101,7 @@ int gmp_decompress_noalloc(const uint8_t* d_comp, size_t comp_bytes, const gmp_b
   gmp_file_desc F{d_comp, comp_bytes, d_index, n_blocks, d_out, out_cap};
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(scratch);
   cudaError_t e = gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, counter, scratch + kHeaderBytes,
-                                     kSlotBytes, kRecBytes, kMaxSeq, kMaxBlockOut, counter + 8, 0, s);
+                                     kSlotBytes, kRecBytes, kMaxSeq, kMaxBlockOut, counter + 8, 0, 0, s);
   return e == cudaSuccess ? GMP_OK : GMP_ERR_CUDA;
 }
 

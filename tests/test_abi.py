@@ -54,6 +54,50 @@ def test_compressor_streams_validate_and_roundtrip(lib):
                 assert r["de_weak_ok"]
 
 
+def test_compressor_byte_streams_validate_and_roundtrip(lib):
+    import paper_1606_00519_gb300 as gmp
+    rnd = np.random.default_rng(9).integers(0, 256, 5000).astype(np.uint8)  # literal strings over 1023 bytes
+    for data in (datagen.csv_records(700_000, seed=5), datagen.markov_text(300_000, seed=6, order=3), rnd):
+        for de in (False, True):
+            s = gmp.compress(data, 64 * 1024, 16, 8192, de=de, byte_mode=True)
+            info = gmp.stream_info(s)
+            assert info.flags == (1 if de else 0) and info.n_sub == 0 and info.cwl == 0
+            r = oracle.validate(s)
+            assert r["rc"] == 0 and r["offsets_ok"] and r["blocks_ok"]
+            assert np.array_equal(oracle.decompress(s), data)
+            if de:
+                assert r["de_weak_ok"]
+
+
+def test_encode_tokens_matches_oracle(lib):
+    import paper_1606_00519_gb300 as gmp
+    for m in (1, 4, 32):
+        ts = datagen.nesting_tokens(seed=300 + m, m=m, n_inst=32 * 20)
+        expect = oracle.lz77_decode(ts.lit_len, ts.mlen, ts.off, ts.lits, 32768)
+        for byte_mode in (False, True):
+            s = gmp.encode_tokens(ts.lit_len, ts.mlen, ts.off, ts.lits, n_sub=16, byte_mode=byte_mode)
+            assert np.array_equal(oracle.decompress(s), expect)
+            # the same parse: the oracle reads back exactly the sequences given
+            got = oracle.block_tokens(s, 0)
+            assert np.array_equal(got.mlen[got.mlen > 0], ts.mlen[ts.mlen > 0])
+            assert np.array_equal(got.off[got.mlen > 0], ts.off[ts.mlen > 0])
+
+
+def test_encode_tokens_rejects_bad_parses(lib):
+    import paper_1606_00519_gb300 as gmp
+    lits = np.frombuffer(b"abcdef", np.uint8)
+    with pytest.raises(gmp.GmpError):  # distance before the block start
+        gmp.encode_tokens([3, 3], [4, 0], [5, 0], lits)
+    with pytest.raises(gmp.GmpError):  # match shorter than 3
+        gmp.encode_tokens([3, 3], [2, 0], [1, 0], lits)
+    with pytest.raises(gmp.GmpError):  # a Huffman block's sequence without a back-reference before the end
+        gmp.encode_tokens([3, 3], [0, 0], [0, 0], lits)
+    with pytest.raises(gmp.GmpError):  # literals left over
+        gmp.encode_tokens([3, 2], [3, 0], [1, 0], lits)
+    s = gmp.encode_tokens([3, 3], [0, 0], [0, 0], lits, byte_mode=True)  # fine in Byte blocks
+    assert bytes(oracle.decompress(s)) == b"abcdef"
+
+
 def test_compressor_tiny_inputs(lib):
     import paper_1606_00519_gb300 as gmp
     for data in (b"", b"x", b"xy", b"aaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaa", bytes(range(256)) * 3):
