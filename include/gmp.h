@@ -301,10 +301,25 @@ int gmp_stats_reset(gmp_context* ctx, void* stream);
 int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device */
 
 /* ------------------------------------------------------------------------ */
-/* Host-to-host convenience (the paper's "(In/Out)" mode, Sec. 5.4): copies a
-   host stream to the device, decodes it and copies the output back.  Uses
-   (and grows) device staging buffers owned by the context.  host_out: out_cap
-   bytes.  *status receives the decoder status.  Synchronous. */
+/* Host-to-host decompression (the paper's "(In/Out)" mode, Sec. 5.4: input
+   and output in host memory, transfers included).  The streams' blocks are
+   cut into pieces, one persistent launch each, run on up to 8 partitions of
+   the context's scratch with their own CUDA streams: a piece's input copy
+   overlaps the decoding of earlier pieces, and its output is copied back as
+   soon as its launch ends, while later pieces still decode.  Host buffers
+   should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to
+   overlap; pageable buffers work but serialise the copies.  Uses (and grows)
+   device staging buffers owned by the context.
+   gmp_decompress_host_batch: n_files streams (host_streams[f], bytes[f]) into
+   host_outs[f] (out_caps[f] bytes each); statuses[f] (host) receives file
+   f's decoder status.  GMP_ERR_CAPACITY if an output buffer is too small or
+   a block exceeds the context's max_block_out.  Synchronous: returns when
+   every output is in host memory; work is ordered after earlier work on
+   `stream` (the input copies run on it) and later work on `stream` is
+   ordered after this call's. */
+int gmp_decompress_host_batch(gmp_context* ctx, size_t n_files, const void* const* host_streams, const size_t* bytes,
+                              void* const* host_outs, const size_t* out_caps, int32_t* statuses, void* stream);
+/* One stream: host_out holds out_cap bytes; *status receives the status. */
 int gmp_decompress_host(gmp_context* ctx, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,
                         int32_t* status, void* stream);
 

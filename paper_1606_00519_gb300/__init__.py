@@ -255,8 +255,27 @@ class Context:
             d[k] = [int(x) for x in getattr(s, k)]
         return d
 
+    def decompress_host_batch(self, streams, outs=None, cuda_stream=None):
+        """Host streams in, host bytes out: one pipelined call (input copies,
+        decoding and copies back overlap; pinned buffers overlap best).
+        Returns (outputs, statuses)."""
+        ss = [_np_bytes(x) for x in streams]
+        infos = [stream_info(x) for x in ss]
+        if outs is None:
+            outs = [np.empty(max(i.orig_size, 1), np.uint8) for i in infos]
+        n = len(ss)
+        ins = (ctypes.c_void_p * n)(*[x.ctypes.data for x in ss])
+        sizes = (ctypes.c_size_t * n)(*[x.size for x in ss])
+        optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+        caps = (ctypes.c_size_t * n)(*[o.size for o in outs])
+        st = (ctypes.c_int32 * n)()
+        _check(self._L.gmp_decompress_host_batch(self._h, n, ins, sizes, optr, caps, st,
+                                                 _stream_handle(cuda_stream)), "gmp_decompress_host_batch")
+        return [o[:i.orig_size] for o, i in zip(outs, infos)], [int(x) for x in st]
+
     def decompress_host(self, stream, out: np.ndarray | None = None, cuda_stream=None):
-        """Host stream in, host bytes out (H2D + decode + D2H, synchronous)."""
+        """Host stream in, host bytes out (H2D + decode + D2H, pipelined,
+        synchronous)."""
         s = _np_bytes(stream)
         info = stream_info(s)
         if out is None:

@@ -69,6 +69,12 @@ struct gmp_context {
   gmp_block_ref* h_index = nullptr;
   size_t h_index_cap = 0;
   int32_t* h_status = nullptr;
+  size_t h_status_cap = 0;
+  // pipeline of the host-to-host calls: one stream per scratch partition,
+  // one stream for the copies back, and events between them
+  cudaStream_t pipe[gmp::kPipeParts] = {};
+  cudaStream_t d2h = nullptr;
+  std::vector<cudaEvent_t> events;
 };
 
 struct gmp_graph {
@@ -231,6 +237,10 @@ void gmp_context_destroy(gmp_context* c) {
   if (c->h_out) cudaFree(c->h_out);
   if (c->h_index) cudaFree(c->h_index);
   if (c->h_status) cudaFree(c->h_status);
+  for (cudaStream_t t : c->pipe)
+    if (t) cudaStreamDestroy(t);
+  if (c->d2h) cudaStreamDestroy(c->d2h);
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   delete c;
 }
 
@@ -419,20 +429,67 @@ int gmp_stats_read(gmp_context* c, gmp_stats* out) {
   return GMP_OK;
 }
 
-int gmp_decompress_host(gmp_context* c, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,
-                        int32_t* status, void* stream) {
-  if (!c || !host_stream || !status || (!host_out && out_cap)) return GMP_ERR_INVALID_ARG;
+int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const* host_streams, const size_t* bytes,
+                              void* const* host_outs, const size_t* out_caps, int32_t* statuses, void* stream) {
+  if (!c || (n_files && (!host_streams || !bytes || !host_outs || !out_caps || !statuses))) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  size_t nb = 0;
-  gmp_stream_info info;
-  int rc = gmp_index_build(host_stream, bytes, nullptr, 0, &nb, &info);
-  if (rc) return rc;
-  if (info.orig_size > out_cap) return GMP_ERR_CAPACITY;
-  std::vector<gmp_block_ref> idx(nb);
-  rc = gmp_index_build(host_stream, bytes, idx.data(), nb, &nb, &info);
-  if (rc) return rc;
-  if (info.max_block_out > c->max_out) return GMP_ERR_CAPACITY;
+  // ---- parse every stream; lay out the device staging
+  struct File {
+    std::vector<gmp_block_ref> idx;
+    gmp_stream_info info;
+    uint64_t comp_off, out_off, idx_off;
+  };
+  std::vector<File> files;
+  uint64_t comp_total = 0, out_total = 0, n_total = 0;
+  try {
+    files.resize(n_files);
+    for (size_t f = 0; f < n_files; f++) {
+      if (!host_streams[f] || (!host_outs[f] && out_caps[f])) return GMP_ERR_INVALID_ARG;
+      size_t nb = 0;
+      int rc = gmp_index_build(host_streams[f], bytes[f], nullptr, 0, &nb, &files[f].info);
+      if (rc) return rc;
+      files[f].idx.resize(nb);
+      rc = gmp_index_build(host_streams[f], bytes[f], files[f].idx.data(), nb, &nb, &files[f].info);
+      if (rc) return rc;
+      if (files[f].info.orig_size > out_caps[f] || files[f].info.max_block_out > c->max_out) return GMP_ERR_CAPACITY;
+      files[f].comp_off = comp_total;
+      files[f].out_off = out_total;
+      files[f].idx_off = n_total;
+      comp_total += (bytes[f] + 15) & ~uint64_t(15);
+      out_total += (files[f].info.orig_size + 15) & ~uint64_t(15);
+      n_total += nb;
+    }
+  } catch (...) {
+    return GMP_ERR_NOMEM;
+  }
+  // ---- pieces: runs of consecutive blocks of one stream, one launch each.
+  // The scratch's warp slots are cut into kPipeParts partitions; piece j runs
+  // on partition j % kPipeParts (its own stream, work counter and slots), so
+  // up to kPipeParts pieces decode at once and a piece's copy back starts as
+  // soon as its launch ends.  A piece holds at most one partition's warps of
+  // blocks, so each launch is one wave.
+  const uint64_t wpc = (uint64_t)c->shape.warps_per_cta;
+  const uint64_t slots = (uint64_t)c->shape.grid * wpc;
+  uint64_t parts = gmp::kPipeParts;
+  while (parts > 1 && slots / parts < wpc) parts--;
+  const uint64_t part_warps = slots / parts / wpc * wpc;
+  const uint64_t piece_blocks =
+      std::max<uint64_t>(1, std::min<uint64_t>((n_total + parts - 1) / parts, part_warps));
+  struct Piece {
+    size_t file;
+    uint64_t b0, b1;
+  };
+  std::vector<Piece> pieces;
+  try {
+    for (size_t f = 0; f < n_files; f++)
+      for (uint64_t b = 0; b < files[f].idx.size(); b += piece_blocks)
+        pieces.push_back(Piece{f, b, std::min<uint64_t>(files[f].idx.size(), b + piece_blocks)});
+  } catch (...) {
+    return GMP_ERR_NOMEM;
+  }
+  const size_t n_pieces = pieces.size();
+  // ---- staging buffers, streams and events (kept in the context)
   auto grow = [&](auto** p, size_t* cap, size_t need) -> int {
     if (*cap >= need) return GMP_OK;
     if (*p) cudaFree(*p);
@@ -442,18 +499,78 @@ int gmp_decompress_host(gmp_context* c, const void* host_stream, size_t bytes, v
     *cap = need;
     return GMP_OK;
   };
-  if ((rc = grow(&c->h_comp, &c->h_comp_cap, bytes))) return rc;
-  if ((rc = grow(&c->h_out, &c->h_out_cap, std::max<size_t>(info.orig_size, 16)))) return rc;
-  if ((rc = grow(&c->h_index, &c->h_index_cap, std::max<size_t>(nb, 1) * sizeof(gmp_block_ref)))) return rc;
-  if (!c->h_status) GMP_CUDA(cudaMalloc(&c->h_status, 16));
-  GMP_CUDA(cudaMemcpyAsync(c->h_comp, host_stream, bytes, cudaMemcpyHostToDevice, s));
-  if (nb) GMP_CUDA(cudaMemcpyAsync(c->h_index, idx.data(), nb * sizeof(gmp_block_ref), cudaMemcpyHostToDevice, s));
-  rc = gmp_decompress(c, c->h_comp, bytes, c->h_index, nb, c->h_out, info.orig_size, c->h_status, s);
-  if (rc) return rc;
-  if (info.orig_size) GMP_CUDA(cudaMemcpyAsync(host_out, c->h_out, info.orig_size, cudaMemcpyDeviceToHost, s));
-  GMP_CUDA(cudaMemcpyAsync(status, c->h_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  GMP_CUDA(cudaStreamSynchronize(s));
+  int rc;
+  if ((rc = grow(&c->h_comp, &c->h_comp_cap, std::max<uint64_t>(comp_total, 16)))) return rc;
+  if ((rc = grow(&c->h_out, &c->h_out_cap, std::max<uint64_t>(out_total, 16)))) return rc;
+  if ((rc = grow(&c->h_index, &c->h_index_cap, std::max<uint64_t>(n_total, 1) * sizeof(gmp_block_ref)))) return rc;
+  if ((rc = grow(&c->h_status, &c->h_status_cap, std::max<size_t>(n_pieces, 1) * sizeof(int32_t)))) return rc;
+  for (uint64_t k = 0; k < parts; k++)
+    if (!c->pipe[k]) GMP_CUDA(cudaStreamCreateWithFlags(&c->pipe[k], cudaStreamNonBlocking));
+  if (!c->d2h) GMP_CUDA(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking));
+  while (c->events.size() < 2 * n_pieces + 1) {
+    cudaEvent_t e;
+    GMP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->events.push_back(e);
+  }
+  // ---- enqueue: block indexes, then per piece its input bytes (on the
+  // caller's stream) and its launch (on its partition's stream) ...
+  for (size_t f = 0; f < n_files; f++)
+    if (!files[f].idx.empty())
+      GMP_CUDA(cudaMemcpyAsync(c->h_index + files[f].idx_off, files[f].idx.data(),
+                               files[f].idx.size() * sizeof(gmp_block_ref), cudaMemcpyHostToDevice, s));
+  for (size_t j = 0; j < n_pieces; j++) {
+    const Piece& q = pieces[j];
+    const File& F = files[q.file];
+    const uint8_t* src = static_cast<const uint8_t*>(host_streams[q.file]);
+    // the first piece of a stream also carries the file header and offset table
+    const uint64_t c0 = q.b0 == 0 ? 0 : F.idx[q.b0].comp_offset;
+    const uint64_t c1 = q.b1 == F.idx.size() ? bytes[q.file] : F.idx[q.b1].comp_offset;
+    GMP_CUDA(cudaMemcpyAsync(c->h_comp + F.comp_off + c0, src + c0, c1 - c0, cudaMemcpyHostToDevice, s));
+    GMP_CUDA(cudaEventRecord(c->events[2 * j], s));
+    const uint64_t k = j % parts;
+    cudaStream_t t = c->pipe[k];
+    GMP_CUDA(cudaStreamWaitEvent(t, c->events[2 * j], 0));
+    GMP_CUDA(cudaMemsetAsync(c->h_status + j, 0, sizeof(int32_t), t));
+    unsigned long long* counter = c->counter + 48 + k;
+    GMP_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), t));
+    gmp_file_desc D{c->h_comp + F.comp_off, bytes[q.file], c->h_index + F.idx_off + q.b0, q.b1 - q.b0,
+                    c->h_out + F.out_off, F.info.orig_size};
+    gmp::LaunchShape shape = c->shape;
+    shape.grid = (int)std::min<uint64_t>((q.b1 - q.b0 + wpc - 1) / wpc, part_warps / wpc);
+    GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &D, c->h_status + j, counter,
+                                c->scratch + k * part_warps * c->slot_bytes, c->slot_bytes, c->shadow_off,
+                                c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats, (int)c->opts.resolve,
+                                t));
+    GMP_CUDA(cudaEventRecord(c->events[2 * j + 1], t));
+  }
+  // ... then the copies back, each after its piece's launch
+  for (size_t j = 0; j < n_pieces; j++) {
+    const Piece& q = pieces[j];
+    const File& F = files[q.file];
+    const uint64_t o0 = F.idx[q.b0].out_offset;
+    const uint64_t o1 = F.idx[q.b1 - 1].out_offset + F.idx[q.b1 - 1].out_bytes;
+    GMP_CUDA(cudaStreamWaitEvent(c->d2h, c->events[2 * j + 1], 0));
+    if (o1 > o0)
+      GMP_CUDA(cudaMemcpyAsync(static_cast<uint8_t*>(host_outs[q.file]) + o0, c->h_out + F.out_off + o0, o1 - o0,
+                               cudaMemcpyDeviceToHost, c->d2h));
+  }
+  std::vector<int32_t> st(std::max<size_t>(n_pieces, 1), 0);
+  if (n_pieces)
+    GMP_CUDA(cudaMemcpyAsync(st.data(), c->h_status, n_pieces * sizeof(int32_t), cudaMemcpyDeviceToHost, c->d2h));
+  GMP_CUDA(cudaStreamSynchronize(c->d2h));
+  // the caller's stream: ordered after this call's work
+  GMP_CUDA(cudaEventRecord(c->events[2 * n_pieces], c->d2h));
+  GMP_CUDA(cudaStreamWaitEvent(s, c->events[2 * n_pieces], 0));
+  for (size_t f = 0; f < n_files; f++) statuses[f] = 0;
+  for (size_t j = 0; j < n_pieces; j++)
+    if (st[j] && !statuses[pieces[j].file]) statuses[pieces[j].file] = st[j];
   return GMP_OK;
+}
+
+int gmp_decompress_host(gmp_context* c, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,
+                        int32_t* status, void* stream) {
+  if (!c || !host_stream || !status || (!host_out && out_cap)) return GMP_ERR_INVALID_ARG;
+  return gmp_decompress_host_batch(c, 1, &host_stream, &bytes, &host_out, &out_cap, status, stream);
 }
 
 }  // extern "C"

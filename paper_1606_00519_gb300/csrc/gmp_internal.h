@@ -34,6 +34,9 @@ constexpr uint32_t kBlockFixed = 192;
 constexpr uint32_t kMaxSub = 64;
 constexpr uint32_t kLitLenSyms = 319;
 constexpr uint32_t kOffsetSyms = 30;
+// scratch partitions of the pipelined host-to-host calls (work counters
+// 48..63 of a context)
+constexpr uint32_t kPipeParts = 8;
 
 }  // namespace gmp
 

@@ -1,0 +1,107 @@
+"""GPU tests of the host-to-host calls (the paper's "(In/Out)" mode): streams
+in host memory, decoded by pipelined pieces, outputs back in host memory,
+byte for byte against the oracle, with pinned and pageable buffers, many
+pieces per partition, mixed formats, and per-file error status."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(600, method="thread")]
+
+KiB, MiB = 1 << 10, 1 << 20
+
+
+@pytest.fixture(scope="module")
+def gmp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1606_00519_gb300 import _native
+    _native.build()
+    import paper_1606_00519_gb300 as g
+    return g
+
+
+def _pinned(torch, n):
+    return torch.empty(max(n, 1), dtype=torch.uint8).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("size", [0, 1, 4095, 3 * MiB + 17])
+def test_single_stream_sizes(gmp, size):
+    data = datagen.markov_text(size, seed=size + 5, order=3) if size else np.zeros(0, np.uint8)
+    s = gmp.compress(data, 64 * KiB, 16, 32 * KiB, de=True)
+    ctx = gmp.Context(max_block_out=64 * KiB)
+    out, st = ctx.decompress_host(s)
+    assert st == 0 and np.array_equal(out, data)
+    ctx.close()
+
+
+def test_batch_of_mixed_streams_pinned_and_pageable(gmp):
+    import torch
+    streams, datas = [], []
+    for i in range(7):
+        kind = "csv" if i % 2 else "text3"
+        data = datagen.make_data(kind, 700_000 + 99_999 * i, 50 + i)
+        s = gmp.compress(data, 128 * KiB, 32, 32 * KiB, de=(i % 3 == 0), byte_mode=(i % 4 == 1))
+        streams.append(s)
+        datas.append(data)
+    ctx = gmp.Context(max_block_out=128 * KiB, collect_stats=True)
+    ctx.stats_reset()
+    outs, sts = ctx.decompress_host_batch(streams)
+    assert sts == [0] * len(streams)
+    for o, d, s in zip(outs, datas, streams):
+        assert np.array_equal(o, d) and np.array_equal(o, oracle.decompress(s))
+    assert ctx.stats()["blocks"] == sum(gmp.stream_info(s).n_blocks for s in streams)
+    # pinned inputs and outputs
+    pin_in = []
+    for s in streams:
+        p = _pinned(torch, s.size)[:s.size]
+        p[:] = s
+        pin_in.append(p)
+    pin_out = [_pinned(torch, d.size) for d in datas]
+    outs, sts = ctx.decompress_host_batch(pin_in, pin_out)
+    assert sts == [0] * len(streams)
+    for o, d in zip(outs, datas):
+        assert np.array_equal(o, d)
+    ctx.close()
+
+
+def test_many_pieces_per_partition(gmp):
+    # a small launch shape (152 warp slots, 8 partitions of 19) and 4 KiB
+    # blocks: each stream is cut into many one-wave pieces that queue on
+    # their partitions
+    streams, datas = [], []
+    for i in range(3):
+        data = datagen.csv_records(2 * MiB + 1000 * i, seed=70 + i)
+        streams.append(gmp.compress(data, 4 * KiB, 8, 4 * KiB, de=(i == 1)))
+        datas.append(data)
+    ctx = gmp.Context(max_block_out=4 * KiB, warps_per_cta=1, ctas_per_sm=1)
+    for _ in range(2):  # the staging, streams and events are reused
+        outs, sts = ctx.decompress_host_batch(streams)
+        assert sts == [0, 0, 0]
+        for o, d in zip(outs, datas):
+            assert np.array_equal(o, d)
+    ctx.close()
+
+
+def test_per_file_status_and_capacity(gmp):
+    good = datagen.markov_text(500_000, seed=81, order=2)
+    s_good = gmp.compress(good, 64 * KiB, 16, 8 * KiB)
+    bad_data = datagen.markov_text(500_000, seed=82, order=2)
+    s_bad = oracle.compress(bad_data, oracle.params(64 * KiB, 16, 8 * KiB))
+    bo = int(s_bad[64 + 8 * 2:72 + 8 * 2].view(np.uint64)[0])
+    s_bad[bo + 8 + ord("e") // 2] ^= 0x0F if ord("e") % 2 == 0 else 0xF0  # block 2's code lengths break Kraft
+    assert oracle.decompress_status(s_bad) == oracle.BAD_HEADER
+    ctx = gmp.Context(max_block_out=64 * KiB)
+    outs, sts = ctx.decompress_host_batch([s_good, s_bad, s_good])
+    assert sts[0] == 0 and sts[2] == 0 and sts[1] == oracle.BAD_HEADER
+    assert np.array_equal(outs[0], good) and np.array_equal(outs[2], good)
+    with pytest.raises(gmp.GmpError):
+        ctx.decompress_host_batch([s_good], [np.empty(good.size - 1, np.uint8)])
+    small = gmp.Context(max_block_out=16 * KiB)
+    with pytest.raises(gmp.GmpError):  # blocks larger than the context's max_block_out
+        small.decompress_host(s_good)
+    small.close()
+    ctx.close()
