@@ -485,11 +485,11 @@ def _round_profile(gmp, table, n_files, status, stream, block_size, resolve):
 
 
 def run_sweep(args):
-    """Ablation of the LZ77 resolution strategies (Sec. 5.2): Sequential
+    """Ablation of the LZ77 resolution strategies (Sec. 5.1): Sequential
     Copying (SC), Multi-Round Resolution (MRR) and Dependency Elimination
     (DE) on the text and CSV workloads in both stream formats, then MRR and SC
     against the back-reference nesting depth (1..32 dependent copies per
-    32-sequence group; the nesting-depth data sets of Sec. 5.2, one 256 KiB
+    32-sequence group; the nesting-depth data sets of Sec. 5.1, one 256 KiB
     block per file, as many files as --sweep-bytes holds).  Every decoded
     output is compared with the input before it is timed."""
     import torch

@@ -175,7 +175,7 @@ int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* o, void
 /* One-block stream holding a given LZ77 parse (the entropy-coding half of
    the compressor, for callers with their own match finder, and for streams
    with a chosen dependency structure such as the nesting-depth data sets of
-   Sec. 5.2).  Sequence i is lit_len[i] literal bytes, taken in order from
+   Sec. 5.1).  Sequence i is lit_len[i] literal bytes, taken in order from
    lits (n_lits bytes in all), then a back-reference of match_len[i] bytes
    (0 = none) at distance dist[i].  Host arrays.  Checks: match lengths 3 ..
    o->max_match, distances 1 .. min(o->window, bytes before the copy), total
@@ -207,7 +207,7 @@ typedef struct {
    streams with the DE flag in one pass (groups that break the DE property by
    MRR), others by Multi-Round Resolution (Fig. 5, Sec. 4.1).  MRR: MRR even
    for DE streams.  SC: Sequential Copying, one back-reference at a time in
-   sequence order, the paper's baseline (Sec. 5.2).  All give the same bytes;
+   sequence order, the paper's baseline (Sec. 5.1).  All give the same bytes;
    MRR and SC exist to measure the strategies against each other. */
 typedef enum { GMP_RESOLVE_AUTO = 0, GMP_RESOLVE_MRR = 1, GMP_RESOLVE_SC = 2 } gmp_resolve;
 
@@ -290,7 +290,7 @@ int gmp_autotune(gmp_context* ctx, const gmp_file_desc* d_files, size_t n_files,
    resolution.  Per round r (rounds after the 8th in bin 7): back-reference
    bytes copied in round r and groups that ran a round r, so that
    round_bytes[r] / round_groups[r] is the mean bytes resolved per group in
-   round r (the quantity of the paper's bytes-per-round measurement, Sec. 5.2). */
+   round r (the quantity of the paper's bytes-per-round measurement, Sec. 5.1). */
 typedef struct {
   uint64_t groups, rounds, de_fallback_groups, blocks, max_rounds;
   uint64_t cycles_tables, cycles_huffman, cycles_lz77;

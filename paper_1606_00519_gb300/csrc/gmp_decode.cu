@@ -31,7 +31,7 @@
 // MRR reading (the printed algorithm is ambiguous, see the comment at
 // resolve_group): HWM = write position of the lowest pending lane; a lane may
 // copy once min(read_pos + length, write_pos) <= HWM.  For ablation a context
-// can force MRR on DE streams or resolve by Sequential Copying (Sec. 5.2).
+// can force MRR on DE streams or resolve by Sequential Copying (Sec. 5.1).
 //
 // Every read of the compressed stream is bounds-checked; every loop over
 // input data is bounded by sizes checked against the block header; corrupt
@@ -269,7 +269,7 @@ __device__ __forceinline__ void copy_match_global(uint8_t* out_blk, uint32_t rpo
 //    write_pos) <= HWM.  Lane f always qualifies, so every round resolves at
 //    least one lane and a group needs at most 32 rounds; a group whose
 //    back-references do not depend on each other resolves in one round;
-//  RES_SC: Sequential Copying, the baseline of Sec. 5.2: one back-reference
+//  RES_SC: Sequential Copying, the baseline of Sec. 5.1: one back-reference
 //    per round, in sequence order.
 // Returns the number of rounds, or -1 if a round made no progress.  rstat
 // (statistics only, else null): bytes copied in round r and groups reaching

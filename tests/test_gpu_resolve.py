@@ -1,5 +1,5 @@
 """GPU tests of the back-reference resolution strategies (Sec. 4 and the
-ablation of Sec. 5.2): Sequential Copying, Multi-Round Resolution forced on
+ablation of Sec. 5.1): Sequential Copying, Multi-Round Resolution forced on
 any stream, and the default (DE streams in one pass) all give the oracle's
 bytes; their round counts and the bytes-per-round statistics match what the
 strategy and the stream fix."""
