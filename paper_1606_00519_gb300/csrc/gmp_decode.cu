@@ -349,62 +349,70 @@ struct SrcView {
 
 __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v, uint32_t rpos, uint32_t wpos,
                                                  uint32_t ml) {
-  uint32_t i = 0;
   const bool in_ring = rpos >= v.ring_lo;                                      // whole source in the ring
   const bool in_far = !in_ring && rpos >= v.far_lo && rpos + ml <= v.far_hi;   // whole source staged
   if (!(in_ring || in_far)) {
-    for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+    for (uint32_t i = 0; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
     return;
   }
-  // one linear view of the source: byte x at base[(x - off) & mask]
+  // one linear view of the source: byte x at base[(x - off) & mask], word a
+  // (bytes 4a .. 4a + 3 of the view) at base32[a & wmask]; the staging is
+  // 16-byte aligned, so a source's offset within its word is x & 3 either way
   const uint8_t* base = in_ring ? v.ring : v.far;
+  const uint32_t* base32 = reinterpret_cast<const uint32_t*>(base);
   const uint32_t off = in_ring ? 0u : v.far_lo;
   const uint32_t mask = in_ring ? RING_MASK : 0xffffffffu;
-  if (wpos - rpos < 4) {  // distance 1..3 (a ring source): the pattern repeats byte by byte
-    for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
+  const uint32_t wmask = in_ring ? RING_WMASK : 0xffffffffu;
+  const uint32_t dist = wpos - rpos;
+  if (dist < 4) {  // distance 1..3 (a ring source): the pattern repeats byte by byte
+    for (uint32_t i = 0; i < ml; i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
     return;
   }
-  for (; i < ml && ((wpos + i) & 3u); i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
+  // head: the bytes up to the destination's next 4-byte boundary (at most 3),
+  // loaded together, then stored; their sources precede them (distance >= 4).
+  // Loads past a short source read bytes that are not used (the ring wraps,
+  // the staging has room).
+  const uint32_t h = min(ml, (4u - (wpos & 3u)) & 3u);
+  {
+    const uint8_t b0 = base[(rpos - off) & mask], b1 = base[(rpos + 1u - off) & mask];
+    const uint8_t b2 = base[(rpos + 2u - off) & mask];
+    if (h > 0) ring[wpos & RING_MASK] = b0;
+    if (h > 1) ring[(wpos + 1u) & RING_MASK] = b1;
+    if (h > 2) ring[(wpos + 2u) & RING_MASK] = b2;
+  }
   uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
-  // with a distance of 16 or more, the 16 source bytes of a step lie before
-  // the step's destination, so its five loads issue together (one shared
-  // memory latency per 16 bytes instead of per 4)
-  const bool wide = wpos - rpos >= 16;
-  if (in_ring) {
-    if (wide) {
-      for (; i + 16 <= ml; i += 16) {
-        const uint32_t x = rpos + i, wa = x >> 2, sh = (x & 3u) * 8u, d = (wpos + i) >> 2;
-        const uint32_t w0 = r32[wa & RING_WMASK], w1 = r32[(wa + 1) & RING_WMASK], w2 = r32[(wa + 2) & RING_WMASK];
-        const uint32_t w3 = r32[(wa + 3) & RING_WMASK], w4 = r32[(wa + 4) & RING_WMASK];
-        r32[d & RING_WMASK] = __funnelshift_r(w0, w1, sh);
-        r32[(d + 1) & RING_WMASK] = __funnelshift_r(w1, w2, sh);
-        r32[(d + 2) & RING_WMASK] = __funnelshift_r(w2, w3, sh);
-        r32[(d + 3) & RING_WMASK] = __funnelshift_r(w3, w4, sh);
-      }
-    }
-    for (; i + 4 <= ml; i += 4) {
-      const uint32_t x = rpos + i, wa = x >> 2;
-      r32[((wpos + i) >> 2) & RING_WMASK] =
-          __funnelshift_r(r32[wa & RING_WMASK], r32[(wa + 1) & RING_WMASK], (x & 3u) * 8u);
+  const uint32_t nw = (ml - h) >> 2;  // whole aligned destination words
+  const uint32_t x0 = rpos + h - off, d0 = (wpos + h) >> 2, sh = ((rpos + h) & 3u) * 8u;
+  if (dist >= 16 || in_far) {
+    // four words per step: a step's 16 source bytes lie before its
+    // destination (or in the staging), so its five loads issue together and
+    // a copy of up to 16 bytes takes one shared-memory latency
+    for (uint32_t k = 0; k < nw; k += 4) {
+      const uint32_t a = (x0 >> 2) + k, d = d0 + k;
+      const uint32_t w0 = base32[a & wmask], w1 = base32[(a + 1u) & wmask], w2 = base32[(a + 2u) & wmask];
+      const uint32_t w3 = base32[(a + 3u) & wmask], w4 = base32[(a + 4u) & wmask];
+      r32[d & RING_WMASK] = __funnelshift_r(w0, w1, sh);
+      if (k + 1u < nw) r32[(d + 1u) & RING_WMASK] = __funnelshift_r(w1, w2, sh);
+      if (k + 2u < nw) r32[(d + 2u) & RING_WMASK] = __funnelshift_r(w2, w3, sh);
+      if (k + 3u < nw) r32[(d + 3u) & RING_WMASK] = __funnelshift_r(w3, w4, sh);
     }
   } else {
-    // staged source: a plain array (the reads may run up to one word past
-    // the lane's slot, into other staging; those bytes are discarded)
-    const uint32_t* f32 = reinterpret_cast<const uint32_t*>(v.far);
-    for (; i + 16 <= ml; i += 16) {
-      const uint32_t r = rpos - v.far_lo + i, wa = r >> 2, sh = (r & 3u) * 8u, d = (wpos + i) >> 2;
-      const uint32_t w0 = f32[wa], w1 = f32[wa + 1], w2 = f32[wa + 2], w3 = f32[wa + 3], w4 = f32[wa + 4];
-      r32[d & RING_WMASK] = __funnelshift_r(w0, w1, sh);
-      r32[(d + 1) & RING_WMASK] = __funnelshift_r(w1, w2, sh);
-      r32[(d + 2) & RING_WMASK] = __funnelshift_r(w2, w3, sh);
-      r32[(d + 3) & RING_WMASK] = __funnelshift_r(w3, w4, sh);
-    }
-    for (; i + 4 <= ml; i += 4) {
-      const uint32_t r = rpos - v.far_lo + i;
-      r32[((wpos + i) >> 2) & RING_WMASK] = __funnelshift_r(f32[r >> 2], f32[(r >> 2) + 1], (r & 3u) * 8u);
+    // distance 4..15 in the ring: a source word may hold bytes this copy has
+    // just written, so one word at a time
+    for (uint32_t k = 0; k < nw; k++) {
+      const uint32_t a = (x0 >> 2) + k;
+      r32[(d0 + k) & RING_WMASK] = __funnelshift_r(base32[a & wmask], base32[(a + 1u) & wmask], sh);
     }
   }
-  for (; i < ml; i++) ring[(wpos + i) & RING_MASK] = base[(rpos + i - off) & mask];
+  // tail: fewer than 4 bytes, loaded together (their sources precede them)
+  const uint32_t i = h + 4u * nw, t = ml - i;
+  {
+    const uint8_t b0 = base[(rpos + i - off) & mask], b1 = base[(rpos + i + 1u - off) & mask];
+    const uint8_t b2 = base[(rpos + i + 2u - off) & mask];
+    if (t > 0) ring[(wpos + i) & RING_MASK] = b0;
+    if (t > 1) ring[(wpos + i + 1u) & RING_MASK] = b1;
+    if (t > 2) ring[(wpos + i + 2u) & RING_MASK] = b2;
+  }
 }
 
 // Out-of-line resolutions, kept out of the decode loop's code: Sequential
