@@ -882,10 +882,19 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     int rounds;
     if (fast) {
       const uint32_t ring_lo = max(ring_valid_lo, G0 > NEAR ? G0 - NEAR : 0u);
+      // literal strings, four bytes per step loaded together (the staging
+      // has room for the reads past a string's end; other sources are read
+      // only up to it)
       if (cur.glits) {
         if (cur.lit_staged) {
           const uint8_t* ls = SB.lit[stage] + (lsrc - cur.lit_lo);
-          for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = ls[i];
+          for (uint32_t i = 0; i < ll; i += 4) {
+            const uint8_t b0 = ls[i], b1 = ls[i + 1], b2 = ls[i + 2], b3 = ls[i + 3];
+            ring[(dst + i) & RING_MASK] = b0;
+            if (i + 1 < ll) ring[(dst + i + 1) & RING_MASK] = b1;
+            if (i + 2 < ll) ring[(dst + i + 2) & RING_MASK] = b2;
+            if (i + 3 < ll) ring[(dst + i + 3) & RING_MASK] = b3;
+          }
         } else {
           for (uint32_t i = 0; i < ll; i++) ring[(dst + i) & RING_MASK] = lits[lsrc + i];
         }
