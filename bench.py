@@ -239,6 +239,13 @@ def run_gmp(args):
     table = gmp.make_file_table([ds[m].file_desc(outs[m]) for m in modes], device=dev)
     status = torch.zeros(len(modes), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # launch shape for this workload from the autotuner (outside the timed
+    # region), unless fixed on the command line
+    tuned = None
+    if not args.warps_per_cta:
+        tuned = ctx.autotune(table, len(modes), status, stream)
+    shape = {"warps_per_cta": tuned["warps_per_cta"] if tuned else args.warps_per_cta,
+             "ctas_per_sm": tuned["ctas_per_sm"] if tuned else 0}
     out_bytes = data.size * len(modes)
     comp_bytes = sum(ds[m].comp_bytes for m in modes)
 
@@ -297,8 +304,8 @@ def run_gmp(args):
 
     # where the decode kernel spends its cycles (one extra launch with the
     # per-phase clock counters on, outside the timed region)
-    sctx = gmp.Context(device=local, max_block_out=w.block_size, warps_per_cta=args.warps_per_cta,
-                       collect_stats=True)
+    sctx = gmp.Context(device=local, max_block_out=w.block_size, warps_per_cta=shape["warps_per_cta"],
+                       ctas_per_sm=shape["ctas_per_sm"], collect_stats=True)
     sctx.stats_reset(stream)
     sctx.decompress_batch(table, len(modes), status, stream)
     torch.cuda.synchronize()
@@ -345,7 +352,7 @@ def run_gmp(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {**_config(w, streams, data, args.format), "parallelism": f"replicas x{world}",
-                   "warps_per_cta": args.warps_per_cta or 4, "per_mode_gbs": per_mode,
+                   "launch_shape": {**shape, "autotuned": tuned is not None}, "per_mode_gbs": per_mode,
                    "decode_kernel_cycles": phase_split},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,

@@ -58,10 +58,14 @@ constexpr uint32_t FULL = 0xffffffffu;
 #define GMP_TSTAMP(v)
 #define GMP_TADD(slot, a, b)
 #endif
-constexpr int LUT_BITS = 12;
+constexpr int LUT_BITS = 12;  // the longest code (cwl <= 12)
 constexpr int LUT_SIZE = 1 << LUT_BITS;
-// the offset tree's table covers codes of up to 10 bits; its rare longer codes
-// (11 and 12 bits) are decoded from the canonical arrays kept in S
+// The lookup tables cover codes of up to LL_BITS (literal/length tree) and
+// OFF_BITS (offset tree) bits; the rare longer codes are decoded from the
+// tree's canonical arrays (decode_long).  Small tables keep a warp's shared
+// memory small enough for 20 warps per SM.
+constexpr int LL_BITS = 11;
+constexpr int LL_SIZE = 1 << LL_BITS;
 constexpr int OFF_BITS = 10;
 constexpr int OFF_SIZE = 1 << OFF_BITS;
 constexpr uint16_t LONG_CODE = 0xffff;
@@ -82,6 +86,31 @@ constexpr int FAR_STAGE = 80;
 constexpr int LIT_STAGE = 512;
 constexpr uint32_t RING_WMASK = RING / 4 - 1;
 
+// Canonical arrays of one tree (Sec. 3.1): per code length its code count,
+// its first index in the symbol list sorted by (length, symbol), and its
+// first code.
+struct Canon {
+  uint32_t cnt[16], idx[16], first[16];
+};
+
+// Phase A: the lookup tables, the trees' canonical arrays and the sub-block
+// table of the block being decoded.
+struct PhaseASmem {
+  uint16_t ll[LL_SIZE];
+  uint16_t off[OFF_SIZE];
+  Canon cll, coff;
+  uint32_t run[16];            // LUT build: running rank per length
+  uint32_t sb_bit[MAX_SUB];    // sub-block start bit (from the bitstream start)
+  uint32_t sb_bits[MAX_SUB];   // sub-block size in bits
+  uint32_t sb_out[MAX_SUB];    // sub-block output start (block-relative)
+  uint32_t sb_outn[MAX_SUB];   // sub-block output bytes
+  uint32_t sb_seqn[MAX_SUB];   // sub-block sequence count
+  uint16_t sorted_ll[N_LL + 1];
+  uint16_t sorted_off[N_OFF + 2];
+  uint8_t lens[N_LL + N_OFF + 3];
+};
+
+// Phase B: the output ring and the staging of the next group.
 struct PhaseBSmem {
   uint8_t ring[RING];
   uint8_t far[2][32][FAR_STAGE];
@@ -90,28 +119,15 @@ struct PhaseBSmem {
 
 struct __align__(16) WarpSmem {
   union {
-    struct {
-      uint16_t ll[LUT_SIZE];
-      uint16_t off[OFF_SIZE];
-    } lut;         // phase A
-    PhaseBSmem b;  // phase B
+    PhaseASmem a;
+    PhaseBSmem b;
   } u;
-  uint32_t sb_bit[MAX_SUB];      // sub-block start bit (from the bitstream start)
-  uint32_t sb_bits[MAX_SUB];     // sub-block size in bits
-  uint32_t sb_out[MAX_SUB];      // sub-block output start (block-relative)
-  uint32_t sb_outn[MAX_SUB];     // sub-block output bytes
+  // kept from phase A into phase B
   uint32_t sb_seq[MAX_SUB + 1];  // sub-block first sequence; sb_seq[K] = n_seq
-  uint32_t sb_seqn[MAX_SUB];
   uint32_t sb_lit[MAX_SUB];      // literal count, then literal-source delta
-  uint32_t cnt[16];              // LUT build: code count per length
-  uint32_t idx[16];              // LUT build: first sorted index per length
-  uint32_t first[16];            // LUT build: first canonical code per length
-  uint32_t run[16];              // LUT build: running rank per length
-  uint16_t sorted[N_LL + 1];
-  uint8_t lens[N_LL + N_OFF + 3];
   unsigned long long rstat[16];  // statistics: bytes copied in round r (0..7, 7 = later), groups reaching round r
 };
-static_assert(sizeof(PhaseBSmem) <= (LUT_SIZE + OFF_SIZE) * sizeof(uint16_t), "phase B fits in the LUT space");
+static_assert(sizeof(PhaseASmem) <= sizeof(PhaseBSmem), "phase A fits in the phase B space");
 
 struct KParams {
   const gmp_file_desc* files;  // batch mode; nullptr in single-stream mode
@@ -154,19 +170,20 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
 // TB-bit LSB-first peek e: the code whose bit-reversed value prefixes e,
 // stored as (length << 9) | symbol; 0 = no code (an empty tree); LONG_CODE =
 // the code is longer than TB bits (then decode_long below applies).  Leaves
-// the tree's canonical arrays (cnt, first, idx, sorted) in S.  Returns false
+// the tree's canonical arrays in C and its sorted symbols in `sorted` (run:
+// scratch of 16 words).  Returns false
 // when the code lengths do not form a complete prefix code (Kraft sum != 1)
 // and are not all zero.
 template <int TB>
-__device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut) {
+__device__ bool build_lut(Canon& C, uint32_t* run, uint16_t* sorted, const uint8_t* lens, int n, uint16_t* lut) {
   const uint32_t lane = lane_id();
-  if (lane < 16) { S.cnt[lane] = 0; S.run[lane] = 0; }
+  if (lane < 16) { C.cnt[lane] = 0; run[lane] = 0; }
   __syncwarp();
   for (int base = 0; base < n; base += 32) {
     int s = base + (int)lane;
     uint32_t L = s < n ? lens[s] : 0u;
     uint32_t m = __match_any_sync(FULL, L);
-    if ((__ffs(m) - 1) == (int)lane) S.cnt[L] += __popc(m);
+    if ((__ffs(m) - 1) == (int)lane) C.cnt[L] += __popc(m);
     __syncwarp();
   }
   // Kraft sum and first codes
@@ -175,21 +192,21 @@ __device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut
   if (lane == 0) {
     uint32_t k = 0, code = 0, id = 0;
     for (int L = 1; L <= LUT_BITS; L++) {
-      k += S.cnt[L] << (LUT_BITS - L);
-      S.first[L] = code;
-      S.idx[L] = id;
-      id += S.cnt[L];
-      code = (code + S.cnt[L]) << 1;
+      k += C.cnt[L] << (LUT_BITS - L);
+      C.first[L] = code;
+      C.idx[L] = id;
+      id += C.cnt[L];
+      code = (code + C.cnt[L]) << 1;
     }
     used = id;
     // lengths above 12 have no table slot: such a header is invalid
-    const bool too_long = (S.cnt[13] | S.cnt[14] | S.cnt[15]) != 0;
-    S.idx[0] = (!too_long && (used == 0 || k == (uint32_t)LUT_SIZE)) ? 1u : 0u;  // validity flag
-    S.first[0] = used;
+    const bool too_long = (C.cnt[13] | C.cnt[14] | C.cnt[15]) != 0;
+    C.idx[0] = (!too_long && (used == 0 || k == (uint32_t)LUT_SIZE)) ? 1u : 0u;  // validity flag
+    C.first[0] = used;
   }
   __syncwarp();
-  ok = S.idx[0] != 0;
-  used = S.first[0];
+  ok = C.idx[0] != 0;
+  used = C.first[0];
   if (!ok) return false;
   if (used == 0) {
     for (int e = (int)lane; e < (1 << TB); e += 32) lut[e] = 0;
@@ -202,15 +219,15 @@ __device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut
     uint32_t L = s < n ? lens[s] : 0u;
     uint32_t m = __match_any_sync(FULL, L);
     uint32_t r = __popc(m & ((1u << lane) - 1u));
-    if (L) S.sorted[S.idx[L] + S.run[L] + r] = (uint16_t)s;
+    if (L) sorted[C.idx[L] + run[L] + r] = (uint16_t)s;
     __syncwarp();
-    if (r == 0) S.run[L] += __popc(m);
+    if (r == 0) run[L] += __popc(m);
     __syncwarp();
   }
   // limits of each length's code range, left-justified to TB bits
   uint32_t lim[TB + 1];
 #pragma unroll
-  for (int L = 1; L <= TB; L++) lim[L] = (S.first[L] + S.cnt[L]) << (TB - L);
+  for (int L = 1; L <= TB; L++) lim[L] = (C.first[L] + C.cnt[L]) << (TB - L);
   for (int e = (int)lane; e < (1 << TB); e += 32) {
     uint32_t v = __brev((uint32_t)e) >> (32 - TB);  // peek bits, most significant first
     uint32_t L = 1;
@@ -219,7 +236,7 @@ __device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut
     if (L > (uint32_t)TB) {
       lut[e] = LONG_CODE;
     } else {
-      uint32_t sym = S.sorted[S.idx[L] + (v >> (TB - L)) - S.first[L]];
+      uint32_t sym = sorted[C.idx[L] + (v >> (TB - L)) - C.first[L]];
       lut[e] = (uint16_t)((L << 9) | sym);
     }
   }
@@ -231,11 +248,11 @@ __device__ bool build_lut(WarpSmem& S, const uint8_t* lens, int n, uint16_t* lut
 // peek, most significant bit first, lies in length L's range [first_L,
 // first_L + cnt_L) shifted left by 12 - L.  Returns (L << 9) | symbol.
 template <int TB>
-__device__ __forceinline__ uint32_t decode_long(const WarpSmem& S, uint32_t peek12) {
+__device__ __forceinline__ uint32_t decode_long(const Canon& C, const uint16_t* sorted, uint32_t peek12) {
   const uint32_t v = __brev(peek12) >> (32 - LUT_BITS);
   for (int L = TB + 1; L <= LUT_BITS; L++) {
     const uint32_t code = v >> (LUT_BITS - L);
-    if (code - S.first[L] < S.cnt[L]) return ((uint32_t)L << 9) | S.sorted[S.idx[L] + code - S.first[L]];
+    if (code - C.first[L] < C.cnt[L]) return ((uint32_t)L << 9) | sorted[C.idx[L] + code - C.first[L]];
   }
   return 0;
 }
@@ -551,12 +568,12 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         }
         uint32_t ib = warp_incl_scan(nb), io = warp_incl_scan(no), is = warp_incl_scan(ns);
         if (j < K) {
-          S.sb_bit[j] = carry_bit + ib - nb;
-          S.sb_bits[j] = nb;
-          S.sb_out[j] = carry_out + io - no;
-          S.sb_outn[j] = no;
+          S.u.a.sb_bit[j] = carry_bit + ib - nb;
+          S.u.a.sb_bits[j] = nb;
+          S.u.a.sb_out[j] = carry_out + io - no;
+          S.u.a.sb_outn[j] = no;
           S.sb_seq[j] = carry_seq + is - ns;
-          S.sb_seqn[j] = ns;
+          S.u.a.sb_seqn[j] = ns;
         }
         // sizes are checked below against 64-bit totals, so a wrapped 32-bit
         // sum cannot pass: the totals are bounded by out_bytes / n_seq.
@@ -592,13 +609,12 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       uint32_t sym = i < (uint32_t)N_LL ? i : i - N_LL;
       uint32_t byte = i < (uint32_t)N_LL ? 8 + (sym >> 1) : 168 + (sym >> 1);
       uint8_t v = __ldg(B + byte);
-      S.lens[i] = (sym & 1) ? (v >> 4) : (v & 15);
+      S.u.a.lens[i] = (sym & 1) ? (v >> 4) : (v & 15);
     }
     __syncwarp();
-    bool ok1 = build_lut<LUT_BITS>(S, S.lens, N_LL, S.u.lut.ll);
-    // the offset tree is built last, so its canonical arrays stay in S for
-    // decode_long
-    bool ok2 = build_lut<OFF_BITS>(S, S.lens + N_LL, N_OFF, S.u.lut.off);
+    PhaseASmem& SA = S.u.a;
+    const bool ok1 = build_lut<LL_BITS>(SA.cll, SA.run, SA.sorted_ll, SA.lens, N_LL, SA.ll);
+    const bool ok2 = build_lut<OFF_BITS>(SA.coff, SA.run, SA.sorted_off, SA.lens + N_LL, N_OFF, SA.off);
     if (!ok1 || !ok2) {
       if (lane == 0) set_status(status, GMP_STATUS_BAD_HEADER);
       return;
@@ -641,8 +657,8 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         return w;
       };
       if (act) {
-        pos = S.sb_bit[j];
-        end = pos + S.sb_bits[j];
+        pos = S.u.a.sb_bit[j];
+        end = pos + S.u.a.sb_bits[j];
         // the stash starts with chunk c0 minus the words before the start word
         const uint32_t w0 = pos >> 5, c0 = w0 >> 2;
         const uint4 c = ld4(c0);
@@ -659,12 +675,12 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         nb = 32 - (int)(pos & 31u);
         buf |= (uint64_t)next_word() << nb;
         nb += 32;
-        outp = S.sb_out[j];
-        out_end = outp + S.sb_outn[j];
-        lit_dst = ((S.sb_out[j] + 15u) & ~15u) + 16u * j;
-        lit_lim = lit_dst + S.sb_outn[j];  // first byte past the lane's literal region
+        outp = S.u.a.sb_out[j];
+        out_end = outp + S.u.a.sb_outn[j];
+        lit_dst = ((S.u.a.sb_out[j] + 15u) & ~15u) + 16u * j;
+        lit_lim = lit_dst + S.u.a.sb_outn[j];  // first byte past the lane's literal region
         q = S.sb_seq[j];
-        q_end = q + S.sb_seqn[j];
+        q_end = q + S.u.a.sb_seqn[j];
         act = q < q_end;
       }
       while (__any_sync(FULL, act)) {
@@ -676,7 +692,8 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
             buf |= (uint64_t)next_word() << nb;
             nb += 32;
           }
-          const uint32_t e = S.u.lut.ll[buf & (LUT_SIZE - 1)];
+          uint32_t e = S.u.a.ll[buf & (LL_SIZE - 1)];
+          if (e == LONG_CODE) e = decode_long<LL_BITS>(S.u.a.cll, S.u.a.sorted_ll, (uint32_t)buf & (LUT_SIZE - 1));
           const uint32_t L = e >> 9, sym = e & 511u;
           buf >>= L;
           nb -= (int)L;
@@ -694,8 +711,9 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
                 buf |= (uint64_t)next_word() << nb;
                 nb += 32;
               }
-              uint32_t e2 = S.u.lut.off[buf & (OFF_SIZE - 1)];
-              if (e2 == LONG_CODE) e2 = decode_long<OFF_BITS>(S, (uint32_t)buf & (LUT_SIZE - 1));
+                uint32_t e2 = S.u.a.off[buf & (OFF_SIZE - 1)];
+              if (e2 == LONG_CODE)
+                e2 = decode_long<OFF_BITS>(S.u.a.coff, S.u.a.sorted_off, (uint32_t)buf & (LUT_SIZE - 1));
               const uint32_t L2 = e2 >> 9, os = e2 & 31u;
               const uint32_t ne = os < 4 ? 0u : (os >> 1) - 1u;
               const uint32_t extra = (uint32_t)(buf >> L2) & ((1u << ne) - 1u);
@@ -739,7 +757,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         uint32_t j = base + lane;
         uint32_t n = j < K ? S.sb_lit[j] : 0u;
         uint32_t inc = warp_incl_scan(n);
-        if (j < K) S.sb_lit[j] = (((S.sb_out[j] + 15u) & ~15u) + 16u * j) - (carry + inc - n);
+        if (j < K) S.sb_lit[j] = (((S.u.a.sb_out[j] + 15u) & ~15u) + 16u * j) - (carry + inc - n);
         carry += __shfl_sync(FULL, inc, 31);
       }
     }
@@ -1008,8 +1026,12 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
 // Persistent kernel: warps take work items until none are left.
 // STATS: the statistics build (per-block counters, clocks and round
 // histograms); the other instance carries none of that code.
-template <bool STATS>
-__global__ void __launch_bounds__(32 * 16, 1) decode_kernel(const KParams P) {
+// DEEP: at most 4 warps per CTA and 96 registers per thread, so that 20
+// warps fit per SM (more blocks in flight for inputs of many waves); the
+// other instance keeps 128 registers (16 warps per SM), which makes a single
+// block's decode faster when every block is in flight at once.
+template <bool STATS, bool DEEP>
+__global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(const KParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
@@ -1115,14 +1137,22 @@ namespace gmp {
 size_t warp_smem_bytes() { return sizeof(WarpSmem); }
 
 cudaError_t configure_kernel(size_t smem_bytes) {
-  cudaError_t e =
-      cudaFuncSetAttribute(decode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(decode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  const int b = (int)smem_bytes;
+  cudaError_t e = cudaFuncSetAttribute(decode_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decode_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decode_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(decode_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
 }
 
-cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false>, warps_per_cta * 32,
+cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, bool deep, int* ctas_per_sm) {
+  if (deep)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false, true>, warps_per_cta * 32,
+                                                         smem_bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false, false>, warps_per_cta * 32,
                                                        smem_bytes);
 }
 
@@ -1151,8 +1181,15 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
   // with different shapes may share the process)
   cudaError_t e = configure_kernel(shape.smem_bytes);
   if (e != cudaSuccess) return e;
-  if (collect_stats) decode_kernel<true><<<shape.grid, shape.warps_per_cta * 32, shape.smem_bytes, stream>>>(P);
-  else decode_kernel<false><<<shape.grid, shape.warps_per_cta * 32, shape.smem_bytes, stream>>>(P);
+  const dim3 grid(shape.grid), block(shape.warps_per_cta * 32);
+  const bool deep = shape.deep && shape.warps_per_cta <= 4;
+  if (collect_stats) {
+    if (deep) decode_kernel<true, true><<<grid, block, shape.smem_bytes, stream>>>(P);
+    else decode_kernel<true, false><<<grid, block, shape.smem_bytes, stream>>>(P);
+  } else {
+    if (deep) decode_kernel<false, true><<<grid, block, shape.smem_bytes, stream>>>(P);
+    else decode_kernel<false, false><<<grid, block, shape.smem_bytes, stream>>>(P);
+  }
   return cudaGetLastError();
 }
 

@@ -54,6 +54,7 @@ struct gmp_context {
   int sm_count = 0;
   gmp_context_opts opts{};
   gmp::LaunchShape shape{};
+  int occ_wide = 0, occ_deep = 0;  // CTAs per SM of the two kernels at this shape's warps per CTA
   uint32_t max_seq = 0, max_out = 0;
   uint64_t slot_bytes = 0, shadow_off = 0;
   uint8_t* scratch = nullptr;
@@ -166,13 +167,20 @@ static int context_alloc_scratch(gmp_context* c) {
   if (wpc < 1 || wpc > 16) return GMP_ERR_INVALID_ARG;
   size_t smem = (size_t)wpc * gmp::warp_smem_bytes();
   GMP_CUDA(gmp::configure_kernel(smem));
-  int occ = 0;
-  GMP_CUDA(gmp::occupancy(wpc, smem, &occ));
+  // CTAs per SM of the 128-register kernel and, for CTAs of at most 4 warps,
+  // of the 96-register one; shapes beyond the first need the second
+  int occ_wide = 0, occ_deep = 0;
+  GMP_CUDA(gmp::occupancy(wpc, smem, false, &occ_wide));
+  if (wpc <= 4) GMP_CUDA(gmp::occupancy(wpc, smem, true, &occ_deep));
+  const int occ = std::max(occ_wide, occ_deep);
   if (occ < 1) return GMP_ERR_INVALID_ARG;
   int per_sm = c->opts.ctas_per_sm ? std::min<int>((int)c->opts.ctas_per_sm, occ) : occ;
+  c->occ_wide = occ_wide;
+  c->occ_deep = occ_deep;
   c->shape.grid = per_sm * c->sm_count;
   c->shape.warps_per_cta = wpc;
   c->shape.smem_bytes = smem;
+  c->shape.deep = per_sm > occ_wide;
   // one scratch slot per resident warp: records (8 B per sequence; a block
   // holds at most out/3 + 1 sequences) and the literal shadow (output layout
   // plus 16 bytes of separation per sub-block)
@@ -266,9 +274,10 @@ int gmp_decompress(gmp_context* c, const uint8_t* d_comp, size_t comp_bytes, con
   GMP_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
   gmp_file_desc F{d_comp, comp_bytes, d_index, n_blocks, d_out, out_cap};
   gmp::LaunchShape shape = c->shape;
-  // no more CTAs than work items need
-  uint64_t warps_needed = n_blocks;
-  uint64_t ctas_needed = (warps_needed + shape.warps_per_cta - 1) / shape.warps_per_cta;
+  // no more CTAs than work items need; when the 128-register kernel holds a
+  // warp for every block, it decodes each block faster
+  const uint64_t ctas_needed = (n_blocks + shape.warps_per_cta - 1) / shape.warps_per_cta;
+  if (shape.deep && ctas_needed <= (uint64_t)c->occ_wide * (uint64_t)c->sm_count) shape.deep = false;
   if ((uint64_t)shape.grid > ctas_needed) shape.grid = (int)ctas_needed;
   GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, c->counter, c->scratch, c->slot_bytes,
                               c->shadow_off, c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats,
@@ -353,12 +362,16 @@ int gmp_autotune(gmp_context* c, const gmp_file_desc* d_files, size_t n_files, i
   uint32_t best_w = 0, best_c = 0, tried = 0;
   int rc = GMP_OK;
   for (uint32_t w : {1u, 2u, 4u, 8u, 16u}) {
-    int occ = 0;
+    int occ_wide = 0, occ_deep = 0;
     const size_t smem = (size_t)w * gmp::warp_smem_bytes();
-    if (gmp::configure_kernel(smem) != cudaSuccess || gmp::occupancy((int)w, smem, &occ) != cudaSuccess || occ < 1)
+    if (gmp::configure_kernel(smem) != cudaSuccess || gmp::occupancy((int)w, smem, false, &occ_wide) != cudaSuccess)
       continue;
-    for (int cps : {occ, occ / 2}) {
-      if (cps < 1 || (cps == occ / 2 && occ / 2 == occ)) continue;
+    if (w <= 4 && gmp::occupancy((int)w, smem, true, &occ_deep) != cudaSuccess) occ_deep = 0;
+    // every SM full with the 96-register kernel, full and half full with the
+    // 128-register one
+    const int cands[3] = {occ_deep > occ_wide ? occ_deep : 0, occ_wide, occ_wide / 2};
+    for (int cps : cands) {
+      if (cps < 1 || (cps == occ_wide / 2 && occ_wide / 2 == occ_wide)) continue;
       c->opts.warps_per_cta = w;
       c->opts.ctas_per_sm = (uint32_t)cps;
       if ((rc = context_alloc_scratch(c)) != GMP_OK) break;

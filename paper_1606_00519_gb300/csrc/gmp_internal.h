@@ -15,11 +15,15 @@ struct LaunchShape {
   int grid;           // CTAs of the persistent launch
   int warps_per_cta;  // one block of a stream per warp at a time
   size_t smem_bytes;  // dynamic shared memory per CTA
+  bool deep;          // the 96-register kernel (more than 16 warps per SM; warps_per_cta <= 4)
 };
+
+// warps per SM that the 128-register kernel holds
+constexpr int kWideWarpsPerSm = 16;
 
 size_t warp_smem_bytes();
 cudaError_t configure_kernel(size_t smem_bytes);
-cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, int* ctas_per_sm);
+cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, bool deep, int* ctas_per_sm);
 cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, const uint64_t* item_start,
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,
                           unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,

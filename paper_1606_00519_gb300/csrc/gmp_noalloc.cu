@@ -95,6 +95,7 @@ int gmp_decompress_noalloc(const uint8_t* d_comp, size_t comp_bytes, const gmp_b
   gmp::LaunchShape shape;
   shape.warps_per_cta = (int)kWarpsPerCta;
   shape.smem_bytes = kWarpsPerCta * gmp::warp_smem_bytes();
+  shape.deep = false;
   shape.grid = (int)(kSlots / kWarpsPerCta);
   const uint64_t ctas_needed = (n_blocks + kWarpsPerCta - 1) / kWarpsPerCta;
   if ((uint64_t)shape.grid > ctas_needed) shape.grid = (int)ctas_needed;
