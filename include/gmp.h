@@ -379,7 +379,7 @@ void gmp_server_destroy(gmp_server* s);
    CUDA allocator must not be re-entered, and applications whose memory
    manager owns the whole device.  gmp_decompress needs a context, whose
    creation allocates scratch; this call instead uses a scratch area held in
-   a fixed-size __device__ array of the library (about 31 MB on every GPU that
+   a fixed-size __device__ array of the library (about 53 MB on every GPU that
    loads the library, kept until the process exits).
    Same arguments as gmp_decompress, without a context, plus max_block_out:
    the largest block output of the stream (gmp_stream_info.max_block_out or

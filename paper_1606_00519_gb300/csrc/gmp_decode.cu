@@ -104,6 +104,7 @@ struct PhaseASmem {
   uint32_t sb_bits[MAX_SUB];   // sub-block size in bits
   uint32_t sb_out[MAX_SUB];    // sub-block output start (block-relative)
   uint32_t sb_outn[MAX_SUB];   // sub-block output bytes
+  uint32_t sb_seq[MAX_SUB + 1];  // sub-block first sequence; sb_seq[K] = n_seq
   uint32_t sb_seqn[MAX_SUB];   // sub-block sequence count
   uint16_t sorted_ll[N_LL + 1];
   uint16_t sorted_off[N_OFF + 2];
@@ -122,9 +123,6 @@ struct __align__(16) WarpSmem {
     PhaseASmem a;
     PhaseBSmem b;
   } u;
-  // kept from phase A into phase B
-  uint32_t sb_seq[MAX_SUB + 1];  // sub-block first sequence; sb_seq[K] = n_seq
-  uint32_t sb_lit[MAX_SUB];      // literal count, then literal-source delta
   unsigned long long rstat[16];  // statistics: bytes copied in round r (0..7, 7 = later), groups reaching round r
 };
 static_assert(sizeof(PhaseASmem) <= sizeof(PhaseBSmem), "phase A fits in the phase B space");
@@ -534,19 +532,13 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   }
   // phase A output (Huffman blocks): records and the literal shadow in the
   // warp's scratch slot
-  uint2* rec = reinterpret_cast<uint2*>(slot);
+  uint4* rec = reinterpret_cast<uint4*>(slot);
   uint8_t* shadow = slot + P.shadow_off;
   const uint8_t* lits = shadow;  // phase B's literal source
   long long t_tables, t_phase_a;
   if (byte_fmt) {
-    // one run of sequences: phase B reads the records from the stream and
-    // the literals from the block's literal section
-    if (lane == 0) {
-      S.sb_seq[0] = 0;
-      S.sb_seq[1] = n_seq;
-      S.sb_lit[0] = 0;
-    }
-    K = 1;
+    // phase B reads the records from the stream and the literals from the
+    // block's literal section
     lits = B + lit_off;
     t_tables = t_phase_a = STATS ? clock64() : 0;
     __syncwarp();
@@ -572,7 +564,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
           S.u.a.sb_bits[j] = nb;
           S.u.a.sb_out[j] = carry_out + io - no;
           S.u.a.sb_outn[j] = no;
-          S.sb_seq[j] = carry_seq + is - ns;
+          S.u.a.sb_seq[j] = carry_seq + is - ns;
           S.u.a.sb_seqn[j] = ns;
         }
         // sizes are checked below against 64-bit totals, so a wrapped 32-bit
@@ -581,7 +573,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         carry_out += __shfl_sync(FULL, io, 31);
         carry_seq += __shfl_sync(FULL, is, 31);
       }
-      if (lane == 0) S.sb_seq[K] = carry_seq;
+      if (lane == 0) S.u.a.sb_seq[K] = carry_seq;
       // overflow-safe totals
       uint64_t tb = 0, to = 0, ts = 0;
       for (uint32_t j = lane; j < K; j += 32) {
@@ -679,7 +671,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         out_end = outp + S.u.a.sb_outn[j];
         lit_dst = ((S.u.a.sb_out[j] + 15u) & ~15u) + 16u * j;
         lit_lim = lit_dst + S.u.a.sb_outn[j];  // first byte past the lane's literal region
-        q = S.sb_seq[j];
+        q = S.u.a.sb_seq[j];
         q_end = q + S.u.a.sb_seqn[j];
         act = q < q_end;
       }
@@ -727,7 +719,9 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
             } else if (q + 1 != n_seq) {
               err = GMP_STATUS_CORRUPT_SYMBOL;  // the end symbol only closes the block's last sequence
             }
-            rec[q] = make_uint2(lit_run, (dist << 8) | ml);
+            // the record carries the sequence's output position and literal
+            // source, so that the LZ77 phase needs no prefix sums for it
+            rec[q] = make_uint4(outp - lit_run, lit_dst + nlit - lit_run, lit_run, (dist << 8) | ml);
             q++;
             lit_run = 0;
             outp += ml;
@@ -743,25 +737,11 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       if (j < K) {
         if (!err && pos != end) err = GMP_STATUS_BITSTREAM;
         if (!err && outp != out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
-        S.sb_lit[j] = nlit;
       }
     }
     if (err) set_status(status, err);
     if (__ballot_sync(FULL, err != 0)) return;
     __syncwarp();  // phase A's records and literals are visible to the whole warp
-
-    // literal-source delta per sub-block: shadow start minus literals before it
-    {
-      uint32_t carry = 0;
-      for (uint32_t base = 0; base < K; base += 32) {
-        uint32_t j = base + lane;
-        uint32_t n = j < K ? S.sb_lit[j] : 0u;
-        uint32_t inc = warp_incl_scan(n);
-        if (j < K) S.sb_lit[j] = (((S.u.a.sb_out[j] + 15u) & ~15u) + 16u * j) - (carry + inc - n);
-        carry += __shfl_sync(FULL, inc, 31);
-      }
-    }
-    __syncwarp();
     t_phase_a = STATS ? clock64() : 0;
   }  // Huffman blocks
 
@@ -780,53 +760,58 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   const uint32_t n_groups_total = (n_seq + 31) / 32;
 
   struct Prep {
-    uint32_t ll, ml, dst, lsrc, wpos, rpos, gtot, glits, jnext, far_lo, far_hi, lit_lo, lpre;
+    uint32_t ll, ml, dst, lsrc, wpos, rpos, gtot, glits, far_lo, far_hi, lit_lo;
     int err;  // Byte blocks: the group's records failed a check (a gmp_status)
     bool valid, lit_staged;
   };
-  // sequence t as {literal length, (distance << 8) | match length}; 0 past the end
-  auto load_rec = [&](uint32_t t) -> uint2 {
-    if (t >= n_seq) return make_uint2(0, 0);
+  // sequence t: Huffman blocks {output position, literal source, literal
+  // length, (distance << 8) | match length} from phase A; Byte blocks
+  // {0, 0, literal length, (distance << 8) | match length} from the stream;
+  // zero past the end
+  auto load_rec = [&](uint32_t t) -> uint4 {
+    if (t >= n_seq) return make_uint4(0, 0, 0, 0);
     if (!byte_fmt) return rec[t];
     // match code 63 has no length; it decodes as 65 > max_match and is caught in prep
     const uint32_t r = ld_u32_nc(B + 16 + 4ull * t), m = (r >> 10) & 63u;
-    return make_uint2(r & 1023u, m ? ((((r >> 16) + 1u) << 8) | (m + 2u)) : 0u);
+    return make_uint4(0, 0, r & 1023u, m ? ((((r >> 16) + 1u) << 8) | (m + 2u)) : 0u);
   };
-  // prefix sums and staging of group h; G0h / litposh / jc: where it starts
-  auto prep = [&](uint32_t h, uint2 r, uint32_t G0h, uint32_t litposh, uint32_t jc, bool allow, int stage) {
+  // positions and staging of group h; G0h / litposh: where its output and
+  // (Byte blocks) its literals start
+  auto prep = [&](uint32_t h, uint4 r, uint32_t G0h, uint32_t litposh, bool allow, int stage) {
     Prep q;
     const uint32_t t = h * 32 + lane;
     q.valid = t < n_seq;
-    q.ll = r.x;
-    q.ml = r.y & 0xffu;
-    const uint32_t dist = r.y >> 8;
-    const uint32_t tot = q.ll + q.ml;
-    // one reduction and one scan of (literal length << 16 | total length)
-    // when no lane has 2048 bytes or more (so both halves stay below 2^16),
-    // else two of each
-    uint32_t inc_tot, inc_ll;
-    if (!__any_sync(FULL, tot >= 2048u)) {
-      const uint32_t packed = (q.ll << 16) | tot;
+    q.ll = r.z;
+    q.ml = r.w & 0xffu;
+    const uint32_t dist = r.w >> 8;
+    // the group's literal run in the literal source, [lit_a, lit_b), and
+    // whether the group's literals lie in it back to back
+    uint32_t lit_a, lit_b;
+    bool lit_run;
+    if (!byte_fmt) {
+      q.gtot = __reduce_max_sync(FULL, q.valid ? r.x + q.ll + q.ml : G0h) - G0h;
+      // lanes past the block's last sequence sit at the group's end, so that
+      // write positions never fall with the lane
+      q.dst = q.valid ? r.x : G0h + q.gtot;
+      q.lsrc = r.y;
+      q.glits = __reduce_add_sync(FULL, q.ll);
+      lit_a = __reduce_min_sync(FULL, q.ll ? q.lsrc : 0xffffffffu);
+      lit_b = __reduce_max_sync(FULL, q.ll ? q.lsrc + q.ll : 0u);
+      lit_run = lit_b - lit_a == q.glits;  // one sub-block's literals
+    } else {
+      // one reduction and one scan of (literal length << 16 | total length):
+      // a record's lengths are below 2^11, a group's sums below 2^16
+      const uint32_t packed = (q.ll << 16) | (q.ll + q.ml);
       const uint32_t sum = __reduce_add_sync(FULL, packed);
-      const uint32_t inc = warp_incl_scan(packed);
+      const uint32_t inc = warp_incl_scan(packed) - packed;
       q.gtot = sum & 0xffffu;
       q.glits = sum >> 16;
-      inc_tot = inc & 0xffffu;
-      inc_ll = inc >> 16;
-    } else {
-      q.gtot = __reduce_add_sync(FULL, tot);
-      q.glits = __reduce_add_sync(FULL, q.ll);
-      inc_tot = warp_incl_scan(tot);
-      inc_ll = warp_incl_scan(q.ll);
+      q.dst = G0h + (inc & 0xffffu);
+      q.lsrc = litposh + (inc >> 16);
+      lit_a = litposh;
+      lit_b = litposh + q.glits;
+      lit_run = true;
     }
-    q.lpre = inc_ll - q.ll;
-    q.dst = G0h + inc_tot - tot;
-    // sub-block of the lane's sequence (lanes past the block's end run to
-    // the last sub-block, so lane 31's cursor bounds every valid lane's)
-    uint32_t j = jc;
-    while (j + 1 < K && t >= S.sb_seq[j + 1]) j++;
-    q.lsrc = S.sb_lit[j] + litposh + inc_ll - q.ll;
-    q.jnext = __shfl_sync(FULL, j, 31);
     q.wpos = q.dst + q.ll;
     q.rpos = q.wpos - dist;
     q.far_lo = q.far_hi = 0;
@@ -857,12 +842,12 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
         q.far_hi = a1 > a0 ? a1 : a0;
       }
     }
-    // the group's literals, one contiguous run of the shadow when they all
-    // belong to one sub-block: lane i stages the run's i-th 16-byte chunk
+    // the group's literals, one contiguous run of the literal source when
+    // they all belong to one sub-block: lane i stages the run's i-th 16-byte
+    // chunk
     if (allow && q.glits > 0 && q.gtot <= GROUP_FAST_MAX) {
-      const uint32_t base = S.sb_lit[jc] + litposh;  // lane 0's literal source
-      const uint32_t l0 = base & ~15u, l1 = (base + q.glits + 15u) & ~15u;
-      if (jc == q.jnext && l1 - l0 <= (uint32_t)LIT_STAGE) {
+      const uint32_t l0 = lit_a & ~15u, l1 = (lit_b + 15u) & ~15u;
+      if (lit_run && l1 - l0 <= (uint32_t)LIT_STAGE) {
         const uint32_t c = l0 + 16u * lane;
         if (c < l1) cp_async16(SB.lit[stage] + (c - l0), lits + c);
         q.lit_lo = l0;
@@ -873,8 +858,8 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     return q;
   };
 
-  uint2 r_next = load_rec(lane);
-  Prep cur = prep(0, r_next, 0, 0, 0, true, 0);
+  uint4 r_next = load_rec(lane);
+  Prep cur = prep(0, r_next, 0, 0, true, 0);
   r_next = load_rec(32 + lane);
   for (uint32_t g = 0; g < n_groups_total; g++) {
     if (cur.err) {
@@ -886,7 +871,7 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
     const bool fast = cur.gtot <= GROUP_FAST_MAX;
     // prepare group g+1 (staging only if this group leaves the ring's reach unchanged)
     GMP_TSTAMP(tg0);
-    Prep nxt = prep(g + 1, r_next, G0 + cur.gtot, litpos + cur.glits, cur.jnext, fast, stage ^ 1);
+    Prep nxt = prep(g + 1, r_next, G0 + cur.gtot, litpos + cur.glits, fast, stage ^ 1);
     GMP_TSTAMP(tg1);
     GMP_TADD(0, tg0, tg1);
     r_next = load_rec((g + 2) * 32 + lane);

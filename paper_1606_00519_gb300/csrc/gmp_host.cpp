@@ -181,12 +181,12 @@ static int context_alloc_scratch(gmp_context* c) {
   c->shape.warps_per_cta = wpc;
   c->shape.smem_bytes = smem;
   c->shape.deep = per_sm > occ_wide;
-  // one scratch slot per resident warp: records (8 B per sequence; a block
+  // one scratch slot per resident warp: records (16 B per sequence; a block
   // holds at most out/3 + 1 sequences) and the literal shadow (output layout
   // plus 16 bytes of separation per sub-block)
   c->max_out = c->opts.max_block_out;
   c->max_seq = c->max_out / 3 + 2;
-  uint64_t rec = ((uint64_t)c->max_seq * 8 + 255) & ~255ull;
+  uint64_t rec = ((uint64_t)c->max_seq * 16 + 255) & ~255ull;
   uint64_t shadow = (uint64_t)c->max_out + 16ull * gmp::kMaxSub + 64;
   c->shadow_off = rec;
   c->slot_bytes = (rec + shadow + 255) & ~255ull;

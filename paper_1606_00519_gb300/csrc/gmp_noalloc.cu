@@ -15,7 +15,7 @@
 // Limits: blocks of at most kMaxBlockOut (256 KiB) of output, decoded by
 // kSlots (32) warps at a time.  The array holds one scratch slot per warp plus
 // a header with the work counter; every GPU that loads this library keeps
-// about 31 MB of it until the process exits.
+// about 53 MB of it until the process exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,7 +31,7 @@ constexpr uint32_t kMaxBlockOut = 256u << 10;
 constexpr uint32_t kSlots = 32;
 constexpr uint32_t kWarpsPerCta = 4;
 constexpr uint32_t kMaxSeq = kMaxBlockOut / 3 + 2;
-constexpr uint64_t kRecBytes = ((uint64_t)kMaxSeq * 8 + 255) & ~uint64_t(255);
+constexpr uint64_t kRecBytes = ((uint64_t)kMaxSeq * 16 + 255) & ~uint64_t(255);
 constexpr uint64_t kShadowBytes = (uint64_t)kMaxBlockOut + 16ull * gmp::kMaxSub + 64;
 constexpr uint64_t kSlotBytes = (kRecBytes + kShadowBytes + 255) & ~uint64_t(255);
 constexpr uint64_t kHeaderBytes = 256;  // work counter and statistics words
