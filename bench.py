@@ -634,6 +634,45 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_compress(args):
+    """Compression: the GPU parse (gmp_compress_gpu) against the host
+    compressor (gmp_compress, all host threads), host buffer to host buffer,
+    on the workload in both modes and formats; input GB/s and ratio, and the
+    decoded stream checked against the input on the GPU."""
+    import torch
+    import paper_1606_00519_gb300 as gmp
+
+    torch.cuda.set_device(0)
+    w = datagen.WORKLOADS[args.workload]
+    data = w.data(args.size)
+    ctx = gmp.Context(max_block_out=w.block_size)
+    rows = []
+    for fmt in ("bit", "byte"):
+        for mode in ("mrr", "de"):
+            kw = dict(de=(mode == "de"), byte_mode=(fmt == "byte"))
+            res = {}
+            for name, fn in (("gpu", gmp.compress_gpu), ("host", gmp.compress)):
+                fn(data[:1 << 20], w.block_size, w.n_sub, w.window, **kw)  # warm-up
+                reps = max(1, min(args.steps, 3))
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    st = fn(data, w.block_size, w.n_sub, w.window, **kw)
+                sec = (time.perf_counter() - t0) / reps
+                out, status = ctx.decompress(gmp.DeviceStream(st))
+                if status != 0 or not np.array_equal(out.cpu().numpy(), data):
+                    raise SystemExit(f"compress: {name} {fmt} {mode} stream does not decode to the input")
+                res[name] = {"gbs": round(data.size / sec / 1e9, 3), "ratio": round(data.size / st.size, 4)}
+            row = {"format": fmt, "stream": mode, **res}
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    line = {"metric": "compression input GB/s (host buffers)", "unit": "GB/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {data.size // MiB} MiB {w.kind}, {w.block_size // KiB} KiB blocks",
+                       "host_threads": os.cpu_count()},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """Serving: Poisson arrivals of requests (16 KiB..64 MiB, mixed content
     and modes) admitted under a device-memory budget by the continuous-batching
@@ -749,6 +788,7 @@ def main():
     ap.add_argument("--batch-cap", type=int, default=GiB, help="seeded prefix of the file list up to this many bytes "
                                                                  "(0: all files)")
     ap.add_argument("--sweep", action="store_true", help="resolution strategies and nesting-depth sweep")
+    ap.add_argument("--compress", action="store_true", help="GPU parse against host compressor")
     ap.add_argument("--sweep-bytes", type=int, default=256 * MiB)
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the decode step")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -760,6 +800,8 @@ def main():
         args.warmup = 3
     if args.sweep:
         run_sweep(args)
+    elif args.compress:
+        run_compress(args)
     elif args.batch:
         run_batch(args)
     elif args.serve:

@@ -172,6 +172,21 @@ size_t gmp_compress_bound(size_t n, const gmp_compress_opts* o);
 int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* o, void* host_out, size_t cap,
                  size_t* out_bytes);
 
+/* Compression with the LZ77 parse on the GPU `device` (Sec. 3.1: blocks are
+   compressed independently, so all of them at once; Sec. 4.2 for DE).  A
+   CTA per block finds, for 512 positions at a time, the longest match among
+   up to min(o->chain_depth, 64) earlier positions with the same 3-byte
+   prefix hash (input window, chain heads and links in shared memory); a
+   warp per block then parses (lazy evaluation, the DE rule when o->de,
+   1023-byte literal runs for Byte blocks); the host entropy-codes the parse
+   into the same stream format as gmp_compress (o->n_threads threads).
+   Positions of one step do not see each other, so ratios differ slightly
+   from gmp_compress's.  Host buffers; uses about 8 bytes of device memory
+   per input byte, freed before it returns.  Synchronous.  GMP_ERR_CUDA on
+   a CUDA failure (gmp_last_cuda_error). */
+int gmp_compress_gpu(int device, const void* host_in, size_t n, const gmp_compress_opts* o, void* host_out,
+                     size_t cap, size_t* out_bytes);
+
 /* One-block stream holding a given LZ77 parse (the entropy-coding half of
    the compressor, for callers with their own match finder, and for streams
    with a chosen dependency structure such as the nesting-depth data sets of

@@ -22,7 +22,8 @@ BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD, "libgmp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gmp_decode.cu", "gmp_host.cpp", "gmp_compress.cpp", "gmp_server.cpp", "gmp_noalloc.cu"]
+SOURCES = ["gmp_decode.cu", "gmp_host.cpp", "gmp_compress.cpp", "gmp_server.cpp", "gmp_noalloc.cu",
+           "gmp_gpucompress.cu"]
 
 _lock = threading.Lock()
 _lib = None
@@ -143,6 +144,7 @@ def _declare(L):
     L.gmp_compress_bound.restype = sz
     L.gmp_compress.argtypes = [vp, sz, P(CompressOpts), vp, sz, P(sz)]
     L.gmp_encode_tokens.argtypes = [vp, vp, vp, sz, vp, sz, P(CompressOpts), vp, sz, P(sz)]
+    L.gmp_compress_gpu.argtypes = [i32, vp, sz, P(CompressOpts), vp, sz, P(sz)]
     L.gmp_context_opts_default.argtypes = [P(ContextOpts)]
     L.gmp_context_opts_default.restype = None
     L.gmp_context_create.argtypes = [P(vp), i32, P(ContextOpts)]

@@ -409,6 +409,74 @@ bool opts_ok(const gmp_compress_opts& o) {
 
 }  // namespace
 
+namespace gmp {
+
+// Entropy coding and assembly of parses made elsewhere (the GPU match
+// finder): block b's parse is count[b] tokens at tok + first[b], token =
+// {literal length, (distance << 8) | match length}; literals are taken from
+// `in` in order.  Every token is checked against the block (lengths,
+// distances, sizes), so a faulty parse gives GMP_ERR_INVALID_ARG, never a
+// bad stream.  Blocks are encoded on o.n_threads host threads.
+int encode_token_blocks(const uint8_t* in, size_t n, const gmp_compress_opts& o, const ParseToken* tok,
+                        const uint32_t* count, const uint64_t* first, void* host_out, size_t cap, size_t* out_bytes) {
+  if (!opts_ok(o)) return GMP_ERR_INVALID_ARG;
+  const size_t nb = (n + o.block_size - 1) / o.block_size;
+  std::vector<std::vector<uint8_t>> blocks;
+  try {
+    blocks.resize(nb);
+  } catch (...) {
+    return GMP_ERR_NOMEM;
+  }
+  unsigned nt = o.n_threads ? o.n_threads : std::max(1u, std::thread::hardware_concurrency());
+  nt = (unsigned)std::min<size_t>(nt, std::max<size_t>(nb, 1));
+  std::atomic<size_t> next{0};
+  std::atomic<int> failed{GMP_OK};
+  auto worker = [&]() {
+    try {
+      std::vector<Seq> seqs;
+      for (;;) {
+        size_t b = next.fetch_add(1);
+        if (b >= nb || failed.load() != GMP_OK) break;
+        const size_t s0 = b * (size_t)o.block_size;
+        const uint32_t len = (uint32_t)std::min<size_t>(o.block_size, n - s0);
+        const ParseToken* t = tok + first[b];
+        seqs.clear();
+        uint64_t pos = 0;
+        for (uint32_t k = 0; k < count[b]; k++) {
+          const uint32_t ll = t[k].lit_len, ml = t[k].match & 0xffu, d = t[k].match >> 8;
+          const bool bad_match = ml && (ml < 3 || ml > o.max_match || d == 0 || d > o.window || d > pos + ll);
+          const bool bad_end = !ml && !o.byte_mode && k + 1 != count[b];
+          if (bad_match || bad_end || (o.byte_mode && ll > kByteMaxLit) || pos + ll + ml > len) {
+            failed = GMP_ERR_INVALID_ARG;
+            break;
+          }
+          seqs.push_back(Seq{(uint32_t)pos, ll, ml, ml ? d : 0});
+          pos += ll + ml;
+        }
+        if (failed.load() != GMP_OK) break;
+        if (pos != len) {
+          failed = GMP_ERR_INVALID_ARG;
+          break;
+        }
+        if (o.byte_mode) encode_block_byte(in + s0, len, seqs, blocks[b]);
+        else encode_block(in + s0, len, seqs, o, blocks[b]);
+      }
+    } catch (...) {
+      failed = GMP_ERR_NOMEM;
+    }
+  };
+  std::vector<std::thread> th;
+  for (unsigned t = 1; t < nt; t++) th.emplace_back(worker);
+  worker();
+  for (auto& t : th) t.join();
+  if (failed.load() != GMP_OK) return failed.load();
+  return assemble(o, n, blocks, host_out, cap, out_bytes);
+}
+
+bool compress_opts_ok(const gmp_compress_opts& o) { return opts_ok(o); }
+
+}  // namespace gmp
+
 extern "C" {
 
 void gmp_compress_opts_default(gmp_compress_opts* o) {

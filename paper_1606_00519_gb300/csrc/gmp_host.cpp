@@ -49,6 +49,10 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace gmp {
+int cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+}  // namespace gmp
+
 struct gmp_context {
   int device = 0;
   int sm_count = 0;

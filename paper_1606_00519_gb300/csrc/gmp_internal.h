@@ -42,6 +42,17 @@ constexpr uint32_t kOffsetSyms = 30;
 // 48..63 of a context)
 constexpr uint32_t kPipeParts = 8;
 
+// GPU compressor (gmp_gpucompress.cu) and its host half (gmp_compress.cpp):
+// a block's parse as {literal length, (distance << 8) | match length}.
+struct ParseToken {
+  uint32_t lit_len, match;
+};
+int encode_token_blocks(const uint8_t* in, size_t n, const gmp_compress_opts& o, const ParseToken* tok,
+                        const uint32_t* count, const uint64_t* first, void* host_out, size_t cap, size_t* out_bytes);
+bool compress_opts_ok(const gmp_compress_opts& o);
+// records a CUDA failure for gmp_last_cuda_error; returns GMP_ERR_CUDA
+int cuda_error(cudaError_t e, const char* what);
+
 }  // namespace gmp
 
 #endif  // GMP_INTERNAL_H_
