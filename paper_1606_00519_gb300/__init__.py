@@ -90,15 +90,15 @@ def compress(data, block_size: int = 256 << 10, n_sub: int = 32, window: int = 3
 
 def compress_gpu(data, block_size: int = 256 << 10, n_sub: int = 32, window: int = 32768, cwl: int = 12,
                  max_match: int = 64, de: bool = False, n_threads: int = 0, lazy: bool = True,
-                 byte_mode: bool = False, device: int | None = None) -> np.ndarray:
+                 byte_mode: bool = False, device: int | None = None, chain_depth: int = 64) -> np.ndarray:
     """Compress host bytes with the LZ77 parse on the GPU (gmp_compress_gpu):
     same stream format as compress()."""
     L = _native.lib()
     src = _np_bytes(data)
     if device is None:
         device = _torch().cuda.current_device() if _torch().cuda.is_available() else 0
-    o = CompressOpts(block_size, n_sub, window, cwl, max_match, 64, 1 if de else 0, n_threads, 1 if lazy else 0,
-                     1 if byte_mode else 0)
+    o = CompressOpts(block_size, n_sub, window, cwl, max_match, chain_depth, 1 if de else 0, n_threads,
+                     1 if lazy else 0, 1 if byte_mode else 0)
     cap = L.gmp_compress_bound(src.size, ctypes.byref(o))
     out = np.empty(cap, np.uint8)
     n = ctypes.c_size_t()

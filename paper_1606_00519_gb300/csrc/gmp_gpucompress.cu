@@ -136,17 +136,21 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(const uint8_t* in,
 struct ParseState {
   uint32_t glo[32], ghi[32];  // DE: output ranges of the current group's back-references
   uint32_t in_grp;
+  uint32_t lo_min;            // start of the group's first back-reference (~0u: none yet)
 };
 
 // DE rule (Sec. 4.2, as read in gmp_compress): the source bytes before the
 // current position must avoid the group's earlier back-references; the
 // candidate is cut at the first such byte (0 if fewer than 3 bytes remain).
 // The group's ranges rise with their index (empty ranges stand for
-// literal-only sequences), so the scan runs backwards and stops at the first
-// range that ends at or below the source.
+// literal-only sequences): a source that ends below the first of them is
+// free (the common case: most sources lie before the group); otherwise the
+// scan runs backwards and stops at the first range that ends at or below
+// the source.
 __device__ __forceinline__ uint32_t de_cut(const ParseState& st, uint32_t q, uint32_t L, uint32_t D) {
   if (L == 0) return 0;
   const uint32_t src = q - D, src_end = min(src + L, q);
+  if (src_end <= st.lo_min) return L >= 3 ? L : 0u;
   for (int g = (int)st.in_grp - 1; g >= 0; g--) {
     if (st.glo[g] == st.ghi[g]) continue;
     if (st.ghi[g] <= src) break;
@@ -178,15 +182,20 @@ __global__ void __launch_bounds__(32 * kParseWarps) parse_kernel(const uint8_t* 
   uint32_t nt = 0, p = 0, lit_start = 0;
   ParseState st;
   st.in_grp = 0;
+  st.lo_min = ~0u;
   auto emit = [&](uint32_t ll, uint32_t ml, uint32_t d) {
     if (nt < stride) t[nt] = gmp::ParseToken{ll, (d << 8) | ml};
     nt++;
   };
   auto add_to_group = [&](uint32_t lo, uint32_t hi) {
     if (de) {
+      if (lo != hi && st.lo_min == ~0u) st.lo_min = lo;
       st.glo[st.in_grp] = lo;
       st.ghi[st.in_grp] = hi;
-      if (++st.in_grp == 32) st.in_grp = 0;
+      if (++st.in_grp == 32) {
+        st.in_grp = 0;
+        st.lo_min = ~0u;
+      }
     }
   };
   while (p < len) {
