@@ -319,9 +319,10 @@ int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device
 /* Host-to-host decompression (the paper's "(In/Out)" mode, Sec. 5.4: input
    and output in host memory, transfers included).  The streams' blocks are
    cut into pieces, one persistent launch each, run on up to 8 partitions of
-   the context's scratch with their own CUDA streams: a piece's input copy
-   overlaps the decoding of earlier pieces, and its output is copied back as
-   soon as its launch ends, while later pieces still decode.  Host buffers
+   the context's scratch, each with its own CUDA streams for the copy in,
+   the launch and the copy back: a piece's input copy overlaps the decoding
+   of other pieces, and its output is copied back as soon as its launch
+   ends, while other pieces still decode.  Host buffers
    should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to
    overlap; pageable buffers work but serialise the copies.  Uses (and grows)
    device staging buffers owned by the context.
@@ -330,8 +331,8 @@ int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device
    f's decoder status.  GMP_ERR_CAPACITY if an output buffer is too small or
    a block exceeds the context's max_block_out.  Synchronous: returns when
    every output is in host memory; work is ordered after earlier work on
-   `stream` (the input copies run on it) and later work on `stream` is
-   ordered after this call's. */
+   `stream` (the block indexes and stream headers are copied on it first)
+   and later work on `stream` is ordered after this call's. */
 int gmp_decompress_host_batch(gmp_context* ctx, size_t n_files, const void* const* host_streams, const size_t* bytes,
                               void* const* host_outs, const size_t* out_caps, int32_t* statuses, void* stream);
 /* One stream: host_out holds out_cap bytes; *status receives the status. */

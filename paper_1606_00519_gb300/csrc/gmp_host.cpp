@@ -78,7 +78,8 @@ struct gmp_context {
   // pipeline of the host-to-host calls: one stream per scratch partition,
   // one stream for the copies back, and events between them
   cudaStream_t pipe[gmp::kPipeParts] = {};
-  cudaStream_t d2h = nullptr;
+  cudaStream_t h2d[gmp::kPipeParts] = {};
+  cudaStream_t d2h[gmp::kPipeParts] = {};
   std::vector<cudaEvent_t> events;
 };
 
@@ -251,7 +252,10 @@ void gmp_context_destroy(gmp_context* c) {
   if (c->h_status) cudaFree(c->h_status);
   for (cudaStream_t t : c->pipe)
     if (t) cudaStreamDestroy(t);
-  if (c->d2h) cudaStreamDestroy(c->d2h);
+  for (cudaStream_t t : c->d2h)
+    if (t) cudaStreamDestroy(t);
+  for (cudaStream_t t : c->h2d)
+    if (t) cudaStreamDestroy(t);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   delete c;
 }
@@ -521,29 +525,38 @@ int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const*
   if ((rc = grow(&c->h_out, &c->h_out_cap, std::max<uint64_t>(out_total, 16)))) return rc;
   if ((rc = grow(&c->h_index, &c->h_index_cap, std::max<uint64_t>(n_total, 1) * sizeof(gmp_block_ref)))) return rc;
   if ((rc = grow(&c->h_status, &c->h_status_cap, std::max<size_t>(n_pieces, 1) * sizeof(int32_t)))) return rc;
-  for (uint64_t k = 0; k < parts; k++)
+  for (uint64_t k = 0; k < parts; k++) {
     if (!c->pipe[k]) GMP_CUDA(cudaStreamCreateWithFlags(&c->pipe[k], cudaStreamNonBlocking));
-  if (!c->d2h) GMP_CUDA(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking));
-  while (c->events.size() < 2 * n_pieces + 1) {
+    if (!c->d2h[k]) GMP_CUDA(cudaStreamCreateWithFlags(&c->d2h[k], cudaStreamNonBlocking));
+    if (!c->h2d[k]) GMP_CUDA(cudaStreamCreateWithFlags(&c->h2d[k], cudaStreamNonBlocking));
+  }
+  while (c->events.size() < 2 * n_pieces + 2) {
     cudaEvent_t e;
     GMP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->events.push_back(e);
   }
-  // ---- enqueue: block indexes, then per piece its input bytes (on the
-  // caller's stream) and its launch (on its partition's stream) ...
-  for (size_t f = 0; f < n_files; f++)
-    if (!files[f].idx.empty())
-      GMP_CUDA(cudaMemcpyAsync(c->h_index + files[f].idx_off, files[f].idx.data(),
-                               files[f].idx.size() * sizeof(gmp_block_ref), cudaMemcpyHostToDevice, s));
+  // ---- enqueue: block indexes and the streams' headers (on the caller's
+  // stream), then per piece its blocks' bytes (on its partition's copy-in
+  // stream) and its launch (on its partition's stream) ...
+  cudaEvent_t e_start = c->events[2 * n_pieces], e_end = c->events[2 * n_pieces + 1];
+  for (size_t f = 0; f < n_files; f++) {
+    if (files[f].idx.empty()) continue;
+    GMP_CUDA(cudaMemcpyAsync(c->h_index + files[f].idx_off, files[f].idx.data(),
+                             files[f].idx.size() * sizeof(gmp_block_ref), cudaMemcpyHostToDevice, s));
+    GMP_CUDA(cudaMemcpyAsync(c->h_comp + files[f].comp_off, host_streams[f], files[f].idx[0].comp_offset,
+                             cudaMemcpyHostToDevice, s));
+  }
+  GMP_CUDA(cudaEventRecord(e_start, s));
+  for (uint64_t k = 0; k < parts; k++) GMP_CUDA(cudaStreamWaitEvent(c->h2d[k], e_start, 0));
   for (size_t j = 0; j < n_pieces; j++) {
     const Piece& q = pieces[j];
     const File& F = files[q.file];
     const uint8_t* src = static_cast<const uint8_t*>(host_streams[q.file]);
-    // the first piece of a stream also carries the file header and offset table
-    const uint64_t c0 = q.b0 == 0 ? 0 : F.idx[q.b0].comp_offset;
+    const uint64_t c0 = F.idx[q.b0].comp_offset;
     const uint64_t c1 = q.b1 == F.idx.size() ? bytes[q.file] : F.idx[q.b1].comp_offset;
-    GMP_CUDA(cudaMemcpyAsync(c->h_comp + F.comp_off + c0, src + c0, c1 - c0, cudaMemcpyHostToDevice, s));
-    GMP_CUDA(cudaEventRecord(c->events[2 * j], s));
+    cudaStream_t in_s = c->h2d[j % parts];
+    GMP_CUDA(cudaMemcpyAsync(c->h_comp + F.comp_off + c0, src + c0, c1 - c0, cudaMemcpyHostToDevice, in_s));
+    GMP_CUDA(cudaEventRecord(c->events[2 * j], in_s));
     const uint64_t k = j % parts;
     cudaStream_t t = c->pipe[k];
     GMP_CUDA(cudaStreamWaitEvent(t, c->events[2 * j], 0));
@@ -560,24 +573,31 @@ int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const*
                                 t));
     GMP_CUDA(cudaEventRecord(c->events[2 * j + 1], t));
   }
-  // ... then the copies back, each after its piece's launch
+  // ... then the copies back, each after its piece's launch, on one copy
+  // stream per partition so that copies of pieces ending together overlap
   for (size_t j = 0; j < n_pieces; j++) {
     const Piece& q = pieces[j];
     const File& F = files[q.file];
     const uint64_t o0 = F.idx[q.b0].out_offset;
     const uint64_t o1 = F.idx[q.b1 - 1].out_offset + F.idx[q.b1 - 1].out_bytes;
-    GMP_CUDA(cudaStreamWaitEvent(c->d2h, c->events[2 * j + 1], 0));
+    cudaStream_t u = c->d2h[j % parts];
+    GMP_CUDA(cudaStreamWaitEvent(u, c->events[2 * j + 1], 0));
     if (o1 > o0)
       GMP_CUDA(cudaMemcpyAsync(static_cast<uint8_t*>(host_outs[q.file]) + o0, c->h_out + F.out_off + o0, o1 - o0,
-                               cudaMemcpyDeviceToHost, c->d2h));
+                               cudaMemcpyDeviceToHost, u));
+  }
+  // every copy back has ended before the statuses are read
+  for (uint64_t k = 1; k < parts; k++) {
+    GMP_CUDA(cudaEventRecord(e_end, c->d2h[k]));
+    GMP_CUDA(cudaStreamWaitEvent(c->d2h[0], e_end, 0));
   }
   std::vector<int32_t> st(std::max<size_t>(n_pieces, 1), 0);
   if (n_pieces)
-    GMP_CUDA(cudaMemcpyAsync(st.data(), c->h_status, n_pieces * sizeof(int32_t), cudaMemcpyDeviceToHost, c->d2h));
-  GMP_CUDA(cudaStreamSynchronize(c->d2h));
+    GMP_CUDA(cudaMemcpyAsync(st.data(), c->h_status, n_pieces * sizeof(int32_t), cudaMemcpyDeviceToHost, c->d2h[0]));
+  GMP_CUDA(cudaStreamSynchronize(c->d2h[0]));
   // the caller's stream: ordered after this call's work
-  GMP_CUDA(cudaEventRecord(c->events[2 * n_pieces], c->d2h));
-  GMP_CUDA(cudaStreamWaitEvent(s, c->events[2 * n_pieces], 0));
+  GMP_CUDA(cudaEventRecord(e_end, c->d2h[0]));
+  GMP_CUDA(cudaStreamWaitEvent(s, e_end, 0));
   for (size_t f = 0; f < n_files; f++) statuses[f] = 0;
   for (size_t j = 0; j < n_pieces; j++)
     if (st[j] && !statuses[pieces[j].file]) statuses[pieces[j].file] = st[j];
