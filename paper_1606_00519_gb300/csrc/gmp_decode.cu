@@ -4,29 +4,33 @@
 // One persistent launch; each warp repeatedly takes a work item (one block of
 // one stream) from a device counter and decodes it in two phases:
 //
-//  Phase A, Huffman decoding (Sec. 3.2.1): the warp builds the 4096-entry
-//  lookup tables of the block's two canonical trees in shared memory, then
-//  lane j decodes sub-block j (lanes take j, j+32 for K > 32), starting at
-//  the bit offset given by the prefix sum of the stored sub-block sizes.
+//  Phase A, Huffman decoding (Sec. 3.2.1): the warp builds the lookup
+//  tables of the block's two canonical trees in shared memory (2048 and 1024
+//  entries; the rare longer codes are decoded from the canonical arrays),
+//  then lane j decodes sub-block j (lanes take j, j+32 for K > 32), starting
+//  at the bit offset given by the prefix sum of the stored sub-block sizes.
 //  One table lookup per symbol, no tree walk.  Each lane writes its
-//  sequences as 8-byte records {lit_len, (distance << 8) | match_len} and its
-//  literal bytes to the warp's scratch slot (device memory, as in the paper,
-//  where the decoder's token stream goes to device memory).
+//  sequences as 16-byte records {output position, literal source, literal
+//  length, (distance << 8) | match length} and its literal bytes to the
+//  warp's scratch slot (device memory, as in the paper, where the decoder's
+//  token stream goes to device memory).  The lane knows each sequence's
+//  output position and literal source as it decodes it, so the records carry
+//  the results of the two prefix sums of Sec. 3.2.2.
 //
 //  Phase B, LZ77 decompression (Sec. 3.2.2, Sec. 4): the warp walks the
-//  block's sequences 32 at a time, one per lane: an exclusive prefix sum of
-//  (literal length + match length) by shuffle gives each lane's output
-//  position, a second one of the literal lengths its literal source; the
-//  lanes copy their literal strings, then resolve their back-references by
-//  Multi-Round Resolution (Fig. 5) or, for a DE stream (Fig. 7), all in one
-//  pass.  Output bytes go to a 16 KiB ring in shared memory that also serves
-//  recent back-reference sources; completed 16-byte chunks are flushed to the
-//  caller's buffer with coalesced 16-byte stores, so every output byte is
-//  written to device memory once.
+//  block's sequences 32 at a time, one per lane: the lanes copy their
+//  literal strings, then resolve their back-references by Multi-Round
+//  Resolution (Fig. 5) or, for a DE stream (Fig. 7), all in one pass.
+//  Output bytes go to a 4 KiB ring in shared memory that also serves recent
+//  back-reference sources (older ones are staged by cp.async one group
+//  ahead); completed 16-byte chunks are flushed to the caller's buffer with
+//  coalesced 16-byte stores, so every output byte is written to device
+//  memory once.
 //
 //  Byte blocks (Gompresso/Byte, Sec. 3.1) have no phase A: their sequence
 //  records and literal bytes are read by phase B straight from the stream,
-//  with each group's records checked before it is staged or copied.
+//  positions by one shuffle scan per group, with each group's records
+//  checked before it is staged or copied.
 //
 // MRR reading (the printed algorithm is ambiguous, see the comment at
 // resolve_group): HWM = write position of the lowest pending lane; a lane may
