@@ -63,8 +63,8 @@ struct gmp_context {
   uint64_t slot_bytes = 0, shadow_off = 0;
   uint8_t* scratch = nullptr;
   size_t scratch_bytes = 0;
-  unsigned long long* counter = nullptr;  // work counter
-  unsigned long long* stats = nullptr;    // 5 counters
+  unsigned long long* counter = nullptr;  // 64 words: [0] work counter, [48, 56) pipeline partitions' counters
+  unsigned long long* stats = nullptr;    // counter + 16: 32 statistics words (gmp_stats_read)
   uint64_t* item_start = nullptr;         // batch prefix, max_files + 1
   // staging of gmp_decompress_host
   uint8_t* h_comp = nullptr;
