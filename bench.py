@@ -463,7 +463,9 @@ def run_batch(args):
     table = gmp.make_file_table([ds.file_desc(out, ds.orig_size) for ds, out, _ in files])
     status = torch.zeros(len(files), dtype=torch.int32, device="cuda")
     ctx = gmp.Context(max_block_out=bs, max_files=len(files))
-    ctx.set_launch(tuned["warps_per_cta"], tuned["ctas_per_sm"])
+    # the launch shape for the whole batch (the format tuner's shape was
+    # chosen on its sample, a fraction of the batch's blocks)
+    shape = ctx.autotune(table, len(files), status)
     graph = ctx.batch_graph(table, len(files), status)
     stream = torch.cuda.current_stream()
 
@@ -505,7 +507,8 @@ def run_batch(args):
             "config": {"workload": f"batch: {len(files)} files, log-uniform 4 KiB..16 MiB, text/CSV and MRR/DE mixed"
                                    + (f", seeded prefix up to {cap} bytes" if cap else ""),
                        "total_bytes": total, "compressed_bytes": comp_total, "ratio": round(total / comp_total, 4),
-                       "tuned": tuned, "tune_seconds": round(t_tune, 2)},
+                       "tuned": tuned, "tune_seconds": round(t_tune, 2),
+                       "launch_shape": {"warps_per_cta": shape["warps_per_cta"], "ctas_per_sm": shape["ctas_per_sm"]}},
             "one_launch_per_file": {"value": round(total / (per_file_ms / 1e3) / 1e9, 3), "unit": "GB/s",
                                     "ms_per_step": round(per_file_ms, 4)},
             "speedup_vs_one_launch_per_file": round(per_file_ms / graph_ms, 3)}
