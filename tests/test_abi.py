@@ -69,6 +69,43 @@ def test_compressor_byte_streams_validate_and_roundtrip(lib):
                 assert r["de_weak_ok"]
 
 
+def test_index_and_header_checks_for_byte_streams(lib):
+    import paper_1606_00519_gb300 as gmp
+    data = datagen.csv_records(300_000, seed=8)
+    s = gmp.compress(data, 64 * 1024, 16, 8192, byte_mode=True)
+    idx, info = gmp.index_build(s)
+    assert info.n_blocks == 5 and info.n_sub == 0 and info.cwl == 0 and not info.flags & 2
+    assert np.all(idx[:, 0] % 16 == 0) and list(idx[:, 3]) == [65536] * 4 + [300_000 - 4 * 65536]
+    assert np.all(idx[:-1, 0] + idx[:-1, 1] == idx[1:, 0])
+    # a Byte header must not claim sub-blocks or a code length limit
+    for off, val in ((12, 16), (14, 12)):
+        bad = s.copy()
+        bad[off] = val
+        with pytest.raises(gmp.GmpError):
+            gmp.index_build(bad)
+    # and a Huffman header must claim both
+    h = gmp.compress(data, 64 * 1024, 16, 8192)
+    bad = h.copy()
+    bad[12:14] = 0
+    with pytest.raises(gmp.GmpError):
+        gmp.index_build(bad)
+
+
+def test_host_compressor_options(lib):
+    import paper_1606_00519_gb300 as gmp
+    data = datagen.markov_text(400_000, seed=12, order=3)
+    sizes = {}
+    for lazy in (False, True):
+        for depth in (1, 8, 64):
+            s = gmp.compress(data, 128 * 1024, 32, 32768, chain_depth=depth, lazy=lazy)
+            assert np.array_equal(oracle.decompress(s), data)
+            sizes[(lazy, depth)] = s.size
+    # deeper search and lazy evaluation never make this input larger
+    assert sizes[(False, 64)] <= sizes[(False, 1)] and sizes[(True, 64)] <= sizes[(False, 64)]
+    with pytest.raises(gmp.GmpError):
+        gmp.compress(data, 128 * 1024, 32, 32768, cwl=8)  # 319 symbols need 9 bits
+
+
 def test_encode_tokens_matches_oracle(lib):
     import paper_1606_00519_gb300 as gmp
     for m in (1, 4, 32):
