@@ -64,12 +64,10 @@ constexpr uint32_t FULL = 0xffffffffu;
 #endif
 constexpr int LUT_BITS = 12;  // the longest code (cwl <= 12)
 constexpr int LUT_SIZE = 1 << LUT_BITS;
-// The lookup tables cover codes of up to LL_BITS (literal/length tree) and
-// OFF_BITS (offset tree) bits; the rare longer codes are decoded from the
-// tree's canonical arrays (decode_long).  Small tables keep a warp's shared
-// memory small enough for 20 warps per SM.
-constexpr int LL_BITS = 11;
-constexpr int LL_SIZE = 1 << LL_BITS;
+// The lookup tables cover codes of up to LLB (literal/length tree: 12 bits in
+// the 128-register kernel, 11 in the 96-register one, whose 20 warps per SM
+// need a smaller table) and OFF_BITS (offset tree) bits; the rare longer
+// codes are decoded from the tree's canonical arrays (decode_long).
 constexpr int OFF_BITS = 10;
 constexpr int OFF_SIZE = 1 << OFF_BITS;
 constexpr uint16_t LONG_CODE = 0xffff;
@@ -99,8 +97,9 @@ struct Canon {
 
 // Phase A: the lookup tables, the trees' canonical arrays and the sub-block
 // table of the block being decoded.
+template <int LLB>
 struct PhaseASmem {
-  uint16_t ll[LL_SIZE];
+  uint16_t ll[1 << LLB];
   uint16_t off[OFF_SIZE];
   Canon cll, coff;
   uint32_t run[16];            // LUT build: running rank per length
@@ -122,14 +121,15 @@ struct PhaseBSmem {
   uint8_t lit[2][LIT_STAGE];
 };
 
+template <int LLB>
 struct __align__(16) WarpSmem {
   union {
-    PhaseASmem a;
+    PhaseASmem<LLB> a;
     PhaseBSmem b;
   } u;
   unsigned long long rstat[16];  // statistics: bytes copied in round r (0..7, 7 = later), groups reaching round r
 };
-static_assert(sizeof(PhaseASmem) <= sizeof(PhaseBSmem), "phase A fits in the phase B space");
+static_assert(sizeof(PhaseASmem<11>) <= sizeof(PhaseBSmem), "the 11-bit phase A fits in the phase B space");
 
 struct KParams {
   const gmp_file_desc* files;  // batch mode; nullptr in single-stream mode
@@ -467,8 +467,8 @@ __device__ __forceinline__ bool de_group_ok(uint32_t rpos, uint32_t wpos, uint32
 
 // ---------------------------------------------------------------------------
 // Decode one block.  Returns false if an error was recorded.
-template <bool STATS>
-__device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc& F, uint64_t b, int32_t* status,
+template <bool STATS, int LLB>
+__device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_desc& F, uint64_t b, int32_t* status,
                              uint8_t* slot, unsigned long long* st_acc) {
   const uint32_t lane = lane_id();
   const uint8_t* comp = F.comp;
@@ -608,8 +608,8 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
       S.u.a.lens[i] = (sym & 1) ? (v >> 4) : (v & 15);
     }
     __syncwarp();
-    PhaseASmem& SA = S.u.a;
-    const bool ok1 = build_lut<LL_BITS>(SA.cll, SA.run, SA.sorted_ll, SA.lens, N_LL, SA.ll);
+    PhaseASmem<LLB>& SA = S.u.a;
+    const bool ok1 = build_lut<LLB>(SA.cll, SA.run, SA.sorted_ll, SA.lens, N_LL, SA.ll);
     const bool ok2 = build_lut<OFF_BITS>(SA.coff, SA.run, SA.sorted_off, SA.lens + N_LL, N_OFF, SA.off);
     if (!ok1 || !ok2) {
       if (lane == 0) set_status(status, GMP_STATUS_BAD_HEADER);
@@ -683,13 +683,70 @@ __device__ void decode_block(WarpSmem& S, const KParams& P, const gmp_file_desc&
   #ifdef GMP_PHASE_TIMERS
         tdet[5]++;
   #endif
+        // two symbols per lane per warp step (the second only if the lane is
+        // still active), halving the votes and reconvergence points
         if (act) {
           if (nb < 32) {
             buf |= (uint64_t)next_word() << nb;
             nb += 32;
           }
-          uint32_t e = S.u.a.ll[buf & (LL_SIZE - 1)];
-          if (e == LONG_CODE) e = decode_long<LL_BITS>(S.u.a.cll, S.u.a.sorted_ll, (uint32_t)buf & (LUT_SIZE - 1));
+          uint32_t e = S.u.a.ll[buf & ((1u << LLB) - 1u)];
+          if (LLB < LUT_BITS && e == LONG_CODE)
+            e = decode_long<LLB>(S.u.a.cll, S.u.a.sorted_ll, (uint32_t)buf & (LUT_SIZE - 1));
+          const uint32_t L = e >> 9, sym = e & 511u;
+          buf >>= L;
+          nb -= (int)L;
+          pos += L;
+          if (sym < 256) {
+            shadow[min(lit_dst + nlit, lit_lim)] = (uint8_t)sym;  // clamped: a corrupt stream is caught below
+            nlit++;
+            lit_run++;
+            outp++;
+          } else {
+            uint32_t ml = 0, dist = 0;
+            if (sym > 256) {
+              ml = sym - 254u;
+              if (nb < 32) {
+                buf |= (uint64_t)next_word() << nb;
+                nb += 32;
+              }
+                uint32_t e2 = S.u.a.off[buf & (OFF_SIZE - 1)];
+              if (e2 == LONG_CODE)
+                e2 = decode_long<OFF_BITS>(S.u.a.coff, S.u.a.sorted_off, (uint32_t)buf & (LUT_SIZE - 1));
+              const uint32_t L2 = e2 >> 9, os = e2 & 31u;
+              const uint32_t ne = os < 4 ? 0u : (os >> 1) - 1u;
+              const uint32_t extra = (uint32_t)(buf >> L2) & ((1u << ne) - 1u);
+              buf >>= L2 + ne;
+              nb -= (int)(L2 + ne);
+              pos += L2 + ne;
+              dist = os < 4 ? os + 1u : ((2u | (os & 1u)) << ne) + extra + 1u;
+              if (L2 == 0 || os >= (uint32_t)N_OFF || ml > max_match) err = GMP_STATUS_CORRUPT_SYMBOL;
+              else if (dist > window || dist > outp) err = GMP_STATUS_BAD_OFFSET;
+              else if (ml > out_end - min(outp, out_end)) err = GMP_STATUS_OUTPUT_OVERRUN;
+            } else if (q + 1 != n_seq) {
+              err = GMP_STATUS_CORRUPT_SYMBOL;  // the end symbol only closes the block's last sequence
+            }
+            // the record carries the sequence's output position and literal
+            // source, so that the LZ77 phase needs no prefix sums for it
+            rec[q] = make_uint4(outp - lit_run, lit_dst + nlit - lit_run, lit_run, (dist << 8) | ml);
+            q++;
+            lit_run = 0;
+            outp += ml;
+          }
+          // a lane that runs past its sub-block stops here (this bounds the
+          // loop on corrupt input); sizes are checked when the sub-block ends
+          if (L == 0) err = GMP_STATUS_CORRUPT_SYMBOL;
+          else if (pos > end) err = GMP_STATUS_BITSTREAM;
+          act = !err && q < q_end;
+        }
+        if (act) {  // second symbol of the step
+          if (nb < 32) {
+            buf |= (uint64_t)next_word() << nb;
+            nb += 32;
+          }
+          uint32_t e = S.u.a.ll[buf & ((1u << LLB) - 1u)];
+          if (LLB < LUT_BITS && e == LONG_CODE)
+            e = decode_long<LLB>(S.u.a.cll, S.u.a.sorted_ll, (uint32_t)buf & (LUT_SIZE - 1));
           const uint32_t L = e >> 9, sym = e & 511u;
           buf >>= L;
           nb -= (int)L;
@@ -1024,7 +1081,8 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
-  WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
+  constexpr int LLB = DEEP ? 11 : 12;
+  WarpSmem<LLB>& S = reinterpret_cast<WarpSmem<LLB>*>(smem_raw)[warp];
   const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   uint8_t* slot = P.scratch + gw * P.slot_bytes;
   uint64_t total;
@@ -1055,7 +1113,7 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
     } else {
       F = P.single;
     }
-    decode_block<STATS>(S, P, F, b, P.status + file, slot, st_acc);
+    decode_block<STATS, LLB>(S, P, F, b, P.status + file, slot, st_acc);
     __syncwarp();
   }
   if (STATS && lane == 0 && st_acc[3]) {
@@ -1123,17 +1181,19 @@ __global__ void __launch_bounds__(1024) batch_prefix_kernel(const gmp_file_desc*
 
 namespace gmp {
 
-size_t warp_smem_bytes() { return sizeof(WarpSmem); }
+size_t warp_smem_bytes(bool deep) { return deep ? sizeof(WarpSmem<11>) : sizeof(WarpSmem<12>); }
 
-cudaError_t configure_kernel(size_t smem_bytes) {
+cudaError_t configure_kernel(bool deep, size_t smem_bytes) {
   const int b = (int)smem_bytes;
-  cudaError_t e = cudaFuncSetAttribute(decode_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(decode_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(decode_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(decode_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if (deep) {
+    e = cudaFuncSetAttribute(decode_kernel<false, true>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<true, true>, a, b);
+  } else {
+    e = cudaFuncSetAttribute(decode_kernel<false, false>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<true, false>, a, b);
+  }
   return e;
 }
 
@@ -1168,10 +1228,10 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
   P.resolve = resolve;
   // the attribute is per kernel, so set it for this launch's shape (contexts
   // with different shapes may share the process)
-  cudaError_t e = configure_kernel(shape.smem_bytes);
+  const bool deep = shape.deep && shape.warps_per_cta <= 4;
+  cudaError_t e = configure_kernel(deep, shape.smem_bytes);
   if (e != cudaSuccess) return e;
   const dim3 grid(shape.grid), block(shape.warps_per_cta * 32);
-  const bool deep = shape.deep && shape.warps_per_cta <= 4;
   if (collect_stats) {
     if (deep) decode_kernel<true, true><<<grid, block, shape.smem_bytes, stream>>>(P);
     else decode_kernel<true, false><<<grid, block, shape.smem_bytes, stream>>>(P);

@@ -170,13 +170,18 @@ static int context_alloc_scratch(gmp_context* c) {
   // launch shape: persistent grid, as many CTAs per SM as fit
   int wpc = c->opts.warps_per_cta ? (int)c->opts.warps_per_cta : 4;
   if (wpc < 1 || wpc > 16) return GMP_ERR_INVALID_ARG;
-  size_t smem = (size_t)wpc * gmp::warp_smem_bytes();
-  GMP_CUDA(gmp::configure_kernel(smem));
   // CTAs per SM of the 128-register kernel and, for CTAs of at most 4 warps,
-  // of the 96-register one; shapes beyond the first need the second
+  // of the 96-register one (each with its own shared memory per warp);
+  // shapes beyond the first need the second
+  const size_t smem_wide = (size_t)wpc * gmp::warp_smem_bytes(false);
+  const size_t smem_deep = (size_t)wpc * gmp::warp_smem_bytes(true);
   int occ_wide = 0, occ_deep = 0;
-  GMP_CUDA(gmp::occupancy(wpc, smem, false, &occ_wide));
-  if (wpc <= 4) GMP_CUDA(gmp::occupancy(wpc, smem, true, &occ_deep));
+  GMP_CUDA(gmp::configure_kernel(false, smem_wide));
+  GMP_CUDA(gmp::occupancy(wpc, smem_wide, false, &occ_wide));
+  if (wpc <= 4) {
+    GMP_CUDA(gmp::configure_kernel(true, smem_deep));
+    GMP_CUDA(gmp::occupancy(wpc, smem_deep, true, &occ_deep));
+  }
   const int occ = std::max(occ_wide, occ_deep);
   if (occ < 1) return GMP_ERR_INVALID_ARG;
   int per_sm = c->opts.ctas_per_sm ? std::min<int>((int)c->opts.ctas_per_sm, occ) : occ;
@@ -184,8 +189,8 @@ static int context_alloc_scratch(gmp_context* c) {
   c->occ_deep = occ_deep;
   c->shape.grid = per_sm * c->sm_count;
   c->shape.warps_per_cta = wpc;
-  c->shape.smem_bytes = smem;
   c->shape.deep = per_sm > occ_wide;
+  c->shape.smem_bytes = c->shape.deep ? smem_deep : smem_wide;
   // one scratch slot per resident warp: records (16 B per sequence; a block
   // holds at most out/3 + 1 sequences) and the literal shadow (output layout
   // plus 16 bytes of separation per sub-block)
@@ -285,7 +290,10 @@ int gmp_decompress(gmp_context* c, const uint8_t* d_comp, size_t comp_bytes, con
   // no more CTAs than work items need; when the 128-register kernel holds a
   // warp for every block, it decodes each block faster
   const uint64_t ctas_needed = (n_blocks + shape.warps_per_cta - 1) / shape.warps_per_cta;
-  if (shape.deep && ctas_needed <= (uint64_t)c->occ_wide * (uint64_t)c->sm_count) shape.deep = false;
+  if (shape.deep && ctas_needed <= (uint64_t)c->occ_wide * (uint64_t)c->sm_count) {
+    shape.deep = false;
+    shape.smem_bytes = (size_t)shape.warps_per_cta * gmp::warp_smem_bytes(false);
+  }
   if ((uint64_t)shape.grid > ctas_needed) shape.grid = (int)ctas_needed;
   GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, c->counter, c->scratch, c->slot_bytes,
                               c->shadow_off, c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats,
@@ -371,10 +379,14 @@ int gmp_autotune(gmp_context* c, const gmp_file_desc* d_files, size_t n_files, i
   int rc = GMP_OK;
   for (uint32_t w : {1u, 2u, 4u, 8u, 16u}) {
     int occ_wide = 0, occ_deep = 0;
-    const size_t smem = (size_t)w * gmp::warp_smem_bytes();
-    if (gmp::configure_kernel(smem) != cudaSuccess || gmp::occupancy((int)w, smem, false, &occ_wide) != cudaSuccess)
+    const size_t smem_wide = (size_t)w * gmp::warp_smem_bytes(false);
+    const size_t smem_deep = (size_t)w * gmp::warp_smem_bytes(true);
+    if (gmp::configure_kernel(false, smem_wide) != cudaSuccess ||
+        gmp::occupancy((int)w, smem_wide, false, &occ_wide) != cudaSuccess)
       continue;
-    if (w <= 4 && gmp::occupancy((int)w, smem, true, &occ_deep) != cudaSuccess) occ_deep = 0;
+    if (w <= 4 && (gmp::configure_kernel(true, smem_deep) != cudaSuccess ||
+                   gmp::occupancy((int)w, smem_deep, true, &occ_deep) != cudaSuccess))
+      occ_deep = 0;
     // every SM full with the 96-register kernel, full and half full with the
     // 128-register one
     const int cands[3] = {occ_deep > occ_wide ? occ_deep : 0, occ_wide, occ_wide / 2};

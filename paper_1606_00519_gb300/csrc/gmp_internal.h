@@ -21,8 +21,10 @@ struct LaunchShape {
 // warps per SM that the 128-register kernel holds
 constexpr int kWideWarpsPerSm = 16;
 
-size_t warp_smem_bytes();
-cudaError_t configure_kernel(size_t smem_bytes);
+// shared memory per warp of the 128-register (deep = false) and the
+// 96-register (deep = true) kernel
+size_t warp_smem_bytes(bool deep);
+cudaError_t configure_kernel(bool deep, size_t smem_bytes);
 cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, bool deep, int* ctas_per_sm);
 cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, const uint64_t* item_start,
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,

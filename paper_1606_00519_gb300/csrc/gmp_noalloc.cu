@@ -94,7 +94,7 @@ int gmp_decompress_noalloc(const uint8_t* d_comp, size_t comp_bytes, const gmp_b
   if (cudaMemsetAsync(scratch, 0, kHeaderBytes, s) != cudaSuccess) return GMP_ERR_CUDA;
   gmp::LaunchShape shape;
   shape.warps_per_cta = (int)kWarpsPerCta;
-  shape.smem_bytes = kWarpsPerCta * gmp::warp_smem_bytes();
+  shape.smem_bytes = kWarpsPerCta * gmp::warp_smem_bytes(false);
   shape.deep = false;
   shape.grid = (int)(kSlots / kWarpsPerCta);
   const uint64_t ctas_needed = (n_blocks + kWarpsPerCta - 1) / kWarpsPerCta;
