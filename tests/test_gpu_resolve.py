@@ -96,3 +96,29 @@ def test_sc_on_overlapping_and_far_copies(gmp, ctxs):
             for r in ("mrr", "sc"):
                 got, st, _ = decode(gmp, ctxs[r], s)
                 assert st == 0 and np.array_equal(got, data)
+
+
+
+@pytest.mark.parametrize("byte_mode", [False, True])
+def test_chain_of_exactly_adjacent_copies(gmp, ctxs, byte_mode):
+    # each copy's source is exactly the previous copy's output (distance =
+    # previous copy's length + one literal): every 32-sequence group is a
+    # dependency chain of depth 32, the worst case for MRR
+    n = 32 * 40
+    ll = np.ones(n, np.uint32)
+    ml = np.full(n, 16, np.uint32)
+    off = np.full(n, 17, np.uint32)
+    ll[0] = 17  # the first copy takes 16 of the first 17 literals
+    lits = np.random.default_rng(9).integers(0, 256, int(ll.sum())).astype(np.uint8)
+    s = gmp.encode_tokens(ll, ml, off, lits, n_sub=32, byte_mode=byte_mode)
+    expect = oracle.lz77_decode(ll, ml, off, lits)
+    rounds = oracle.mrr_rounds(ll, ml, off, lits)
+    for r in ("auto", "mrr"):
+        got, st, stats = decode(gmp, ctxs[r], s)
+        assert st == 0 and np.array_equal(got, expect), r
+        assert stats["rounds"] == int(rounds.sum()) and stats["max_rounds"] == 32, r
+        assert sum(stats["round_bytes"]) == int(ml.sum()), r
+        # rounds after the 8th land in the last bin
+        assert stats["round_groups"] == [n // 32] * 7 + [25 * (n // 32)], r
+    got, st, stats = decode(gmp, ctxs["sc"], s)
+    assert st == 0 and np.array_equal(got, expect) and stats["rounds"] == n
