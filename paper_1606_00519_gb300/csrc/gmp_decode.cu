@@ -1091,11 +1091,12 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
   unsigned long long st_acc[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (lane < 16) S.rstat[lane] = 0;
   __syncwarp();
-  for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(P.counter, 1ull);
-    item = __shfl_sync(FULL, item, 0);
-    if (item >= total) break;
+  // A warp's first item is fixed and interleaved over the CTAs (warp w of
+  // CTA c takes w * CTAs + c), so that a launch with fewer items than warps
+  // spreads them evenly over the SMs; later items come from the work counter,
+  // numbered after the fixed ones.
+  unsigned long long item = (unsigned long long)warp * gridDim.x + blockIdx.x;
+  while (item < total) {
     uint32_t file = 0;
     uint64_t b = item;
     gmp_file_desc F;
@@ -1115,6 +1116,9 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
     }
     decode_block<STATS, LLB>(S, P, F, b, P.status + file, slot, st_acc);
     __syncwarp();
+    unsigned long long next = 0;
+    if (lane == 0) next = (unsigned long long)gridDim.x * (blockDim.x >> 5) + atomicAdd(P.counter, 1ull);
+    item = __shfl_sync(FULL, next, 0);
   }
   if (STATS && lane == 0 && st_acc[3]) {
     atomicAdd(&P.stats[0], st_acc[0]);

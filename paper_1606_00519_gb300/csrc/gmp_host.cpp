@@ -287,14 +287,18 @@ int gmp_decompress(gmp_context* c, const uint8_t* d_comp, size_t comp_bytes, con
   GMP_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
   gmp_file_desc F{d_comp, comp_bytes, d_index, n_blocks, d_out, out_cap};
   gmp::LaunchShape shape = c->shape;
-  // no more CTAs than work items need; when the 128-register kernel holds a
-  // warp for every block, it decodes each block faster
+  // when the 128-register kernel holds a warp for every block, it decodes
+  // each block faster; at most one CTA per block, and the kernel spreads the
+  // blocks over the CTAs (a CTA's first warp, then its second, ...), so that
+  // a small input does not crowd a few SMs
   const uint64_t ctas_needed = (n_blocks + shape.warps_per_cta - 1) / shape.warps_per_cta;
-  if (shape.deep && ctas_needed <= (uint64_t)c->occ_wide * (uint64_t)c->sm_count) {
+  const uint64_t wide_ctas = (uint64_t)c->occ_wide * (uint64_t)c->sm_count;
+  if (shape.deep && ctas_needed <= wide_ctas) {
     shape.deep = false;
     shape.smem_bytes = (size_t)shape.warps_per_cta * gmp::warp_smem_bytes(false);
+    if ((uint64_t)shape.grid > wide_ctas) shape.grid = (int)wide_ctas;
   }
-  if ((uint64_t)shape.grid > ctas_needed) shape.grid = (int)ctas_needed;
+  if ((uint64_t)shape.grid > n_blocks) shape.grid = (int)n_blocks;
   GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, c->counter, c->scratch, c->slot_bytes,
                               c->shadow_off, c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats,
                               (int)c->opts.resolve, s));
