@@ -1,7 +1,8 @@
 """GPU tests of the host-to-host calls (the paper's "(In/Out)" mode): streams
 in host memory, decoded by pipelined pieces, outputs back in host memory,
 byte for byte against the oracle, with pinned and pageable buffers, many
-pieces per partition, mixed formats, and per-file error status."""
+pieces per partition, mixed formats, unaligned buffers, groups larger than
+the ring, and per-file error status."""
 import numpy as np
 import pytest
 
@@ -104,4 +105,51 @@ def test_per_file_status_and_capacity(gmp):
     with pytest.raises(gmp.GmpError):  # blocks larger than the context's max_block_out
         small.decompress_host(s_good)
     small.close()
+    ctx.close()
+
+
+def _pin_copy(torch, a, offset=0):
+    p = _pinned(torch, a.size + offset)[offset:offset + a.size]
+    p[:] = a
+    return p
+
+
+def test_pinned_buffers_edge_cases(gmp):
+    import torch
+    rng = np.random.default_rng(91)
+    rnd = rng.integers(0, 256, 300_000).astype(np.uint8)  # long literal runs: groups larger than the ring
+    datas = [datagen.markov_text(1_000_000, seed=92, order=3), rnd,
+             np.concatenate([rnd[:50_000], datagen.csv_records(400_000, seed=93)]),
+             np.zeros(0, np.uint8), datagen.csv_records(33_333, seed=94)]
+    streams = [gmp.compress(datas[0], 64 * KiB, 16, 32 * KiB, de=True),
+               gmp.compress(datas[1], 256 * KiB, 32, 32 * KiB),
+               gmp.compress(datas[2], 1000, 4, 1000, byte_mode=True),  # blocks not a multiple of 16 bytes
+               gmp.compress(datas[3], 64 * KiB, 16, 8 * KiB),
+               gmp.compress(datas[4], 64 * KiB, 16, 8 * KiB)]
+    ctx = gmp.Context(max_block_out=256 * KiB, collect_stats=True)
+    pin_in = [_pin_copy(torch, s) for s in streams]
+    for out_offset in (0, 1):  # outputs 16-byte aligned or not
+        pin_out = [_pinned(torch, d.size + 1)[out_offset:out_offset + d.size] for d in datas]
+        for o in pin_out:
+            o[:] = 0xA5
+        ctx.stats_reset()
+        outs, sts = ctx.decompress_host_batch(pin_in, pin_out)
+        assert sts == [0] * len(datas)
+        for o, d in zip(outs, datas):
+            assert np.array_equal(o, d)
+        assert ctx.stats()["blocks"] == sum(gmp.stream_info(s).n_blocks for s in streams)
+    # a stream that is not 16-byte aligned, or pageable outputs
+    mixed_in = [_pin_copy(torch, streams[0], 1)] + pin_in[1:]
+    outs, sts = ctx.decompress_host_batch(mixed_in, [_pinned(torch, d.size) for d in datas])
+    assert sts == [0] * len(datas) and all(np.array_equal(o, d) for o, d in zip(outs, datas))
+    outs, sts = ctx.decompress_host_batch(pin_in, [np.empty(d.size, np.uint8) for d in datas])
+    assert sts == [0] * len(datas) and all(np.array_equal(o, d) for o, d in zip(outs, datas))
+    # per-file status with pinned buffers
+    bad = streams[4].copy()
+    bo = int(bad[64:72].view(np.uint64)[0])
+    bad[bo + 8 + ord("e") // 2] ^= 0x0F if ord("e") % 2 == 0 else 0xF0  # block 0's code lengths break Kraft
+    assert oracle.decompress_status(bad) == oracle.BAD_HEADER
+    outs, sts = ctx.decompress_host_batch([pin_in[0], _pin_copy(torch, bad)],
+                                          [_pinned(torch, datas[0].size), _pinned(torch, datas[4].size)])
+    assert sts == [0, oracle.BAD_HEADER] and np.array_equal(outs[0], datas[0])
     ctx.close()
