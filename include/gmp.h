@@ -216,6 +216,11 @@ typedef struct {
   uint32_t collect_stats;   /* 1: count groups and MRR rounds (small cost) */
   uint32_t max_files;       /* largest n_files of gmp_decompress_batch (default 65536) */
   uint32_t resolve;         /* back-reference resolution, a gmp_resolve (default GMP_RESOLVE_AUTO) */
+  uint32_t concurrent;      /* 1: launches run beside other kernels (a serving loop's overlapping
+                               batches): every warp takes its blocks from the work counter as it
+                               arrives; 0 (default): a warp's first block is fixed, interleaved
+                               over the CTAs, which spreads a launch's blocks evenly over the SMs
+                               when all its CTAs are resident at once */
 } gmp_context_opts;
 
 /* How a context resolves each 32-sequence group's back-references.  AUTO:

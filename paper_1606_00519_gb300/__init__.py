@@ -183,16 +183,19 @@ class Context:
     """A decoder context (scratch for one persistent launch) on one device."""
 
     def __init__(self, device: int | None = None, max_block_out: int = 256 << 10, warps_per_cta: int = 0,
-                 ctas_per_sm: int = 0, collect_stats: bool = False, max_files: int = 65536, resolve: str = "auto"):
+                 ctas_per_sm: int = 0, collect_stats: bool = False, max_files: int = 65536, resolve: str = "auto",
+                 concurrent: bool = False):
         """resolve: "auto" (DE streams in one pass, others by MRR), "mrr" (MRR
-        always) or "sc" (sequential copying, the paper's baseline)."""
+        always) or "sc" (sequential copying, the paper's baseline).
+        concurrent: the context's launches run beside other kernels (warps take
+        every block from the work counter instead of a fixed first block)."""
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the decoder runs only on the GPU")
         self.device = torch.cuda.current_device() if device is None else int(device)
         self._L = _native.lib()
         o = ContextOpts(max_block_out, warps_per_cta, ctas_per_sm, 1 if collect_stats else 0, max_files,
-                        RESOLVE[resolve])
+                        RESOLVE[resolve], 1 if concurrent else 0)
         h = ctypes.c_void_p()
         _check(self._L.gmp_context_create(ctypes.byref(h), self.device, ctypes.byref(o)), "gmp_context_create")
         self._h = h

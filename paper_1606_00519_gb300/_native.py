@@ -101,7 +101,7 @@ class CompressOpts(ctypes.Structure):
 class ContextOpts(ctypes.Structure):
     _fields_ = [("max_block_out", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("collect_stats", ctypes.c_uint32),
-                ("max_files", ctypes.c_uint32), ("resolve", ctypes.c_uint32)]
+                ("max_files", ctypes.c_uint32), ("resolve", ctypes.c_uint32), ("concurrent", ctypes.c_uint32)]
 
 
 class FileDesc(ctypes.Structure):

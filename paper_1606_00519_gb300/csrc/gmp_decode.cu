@@ -145,6 +145,7 @@ struct KParams {
   unsigned long long* stats;  // [groups, rounds, de_fallback, blocks, max_rounds, cycles x3]
   int collect_stats;
   int resolve;  // 0: by the stream's DE flag, 1: MRR always, 2: sequential copying (SC)
+  int spread;   // 1: first items fixed and interleaved over the CTAs; 0: all from the counter
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -1091,11 +1092,20 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
   unsigned long long st_acc[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (lane < 16) S.rstat[lane] = 0;
   __syncwarp();
-  // A warp's first item is fixed and interleaved over the CTAs (warp w of
-  // CTA c takes w * CTAs + c), so that a launch with fewer items than warps
-  // spreads them evenly over the SMs; later items come from the work counter,
-  // numbered after the fixed ones.
-  unsigned long long item = (unsigned long long)warp * gridDim.x + blockIdx.x;
+  // With `spread`, a warp's first item is fixed and interleaved over the
+  // CTAs (warp w of CTA c takes w * CTAs + c), so that a launch with fewer
+  // items than warps spreads them evenly over the SMs; later items come from
+  // the work counter, numbered after the fixed ones.  Without it (launches
+  // that share the GPU, whose CTAs may not all be resident at once) every
+  // item comes from the counter, in the order the warps arrive.
+  const unsigned long long fixed = P.spread ? (unsigned long long)gridDim.x * (blockDim.x >> 5) : 0ull;
+  unsigned long long item = 0;
+  if (P.spread) {
+    item = (unsigned long long)warp * gridDim.x + blockIdx.x;
+  } else {
+    if (lane == 0) item = atomicAdd(P.counter, 1ull);
+    item = __shfl_sync(FULL, item, 0);
+  }
   while (item < total) {
     uint32_t file = 0;
     uint64_t b = item;
@@ -1117,7 +1127,7 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
     decode_block<STATS, LLB>(S, P, F, b, P.status + file, slot, st_acc);
     __syncwarp();
     unsigned long long next = 0;
-    if (lane == 0) next = (unsigned long long)gridDim.x * (blockDim.x >> 5) + atomicAdd(P.counter, 1ull);
+    if (lane == 0) next = fixed + atomicAdd(P.counter, 1ull);
     item = __shfl_sync(FULL, next, 0);
   }
   if (STATS && lane == 0 && st_acc[3]) {
@@ -1213,8 +1223,9 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,
                           unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,
                           uint32_t max_seq, uint32_t max_out, unsigned long long* stats, int collect_stats,
-                          int resolve, cudaStream_t stream) {
+                          int resolve, cudaStream_t stream, int spread) {
   KParams P;
+  P.spread = spread;
   P.files = files;
   P.item_start = item_start;
   P.n_files = n_files;

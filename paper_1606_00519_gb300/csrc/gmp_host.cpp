@@ -164,6 +164,7 @@ void gmp_context_opts_default(gmp_context_opts* o) {
   o->collect_stats = 0;
   o->max_files = 65536;
   o->resolve = GMP_RESOLVE_AUTO;
+  o->concurrent = 0;
 }
 
 static int context_alloc_scratch(gmp_context* c) {
@@ -301,7 +302,7 @@ int gmp_decompress(gmp_context* c, const uint8_t* d_comp, size_t comp_bytes, con
   if ((uint64_t)shape.grid > n_blocks) shape.grid = (int)n_blocks;
   GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &F, d_status, c->counter, c->scratch, c->slot_bytes,
                               c->shadow_off, c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats,
-                              (int)c->opts.resolve, s));
+                              (int)c->opts.resolve, s, c->opts.concurrent ? 0 : 1));
   return GMP_OK;
 }
 
@@ -317,7 +318,7 @@ int gmp_decompress_batch(gmp_context* c, const gmp_file_desc* d_files, size_t n_
   GMP_CUDA(gmp::launch_batch_prefix(d_files, (uint32_t)n_files, c->item_start, s));
   GMP_CUDA(gmp::launch_decode(c->shape, d_files, c->item_start, (uint32_t)n_files, nullptr, d_status, c->counter,
                               c->scratch, c->slot_bytes, c->shadow_off, c->max_seq, c->max_out, c->stats,
-                              (int)c->opts.collect_stats, (int)c->opts.resolve, s));
+                              (int)c->opts.collect_stats, (int)c->opts.resolve, s, c->opts.concurrent ? 0 : 1));
   return GMP_OK;
 }
 

@@ -30,7 +30,7 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,
                           unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,
                           uint32_t max_seq, uint32_t max_out, unsigned long long* stats, int collect_stats,
-                          int resolve, cudaStream_t stream);
+                          int resolve, cudaStream_t stream, int spread = 1);
 cudaError_t launch_batch_prefix(const gmp_file_desc* files, uint32_t n_files, uint64_t* item_start,
                                 cudaStream_t stream);
 

@@ -303,6 +303,7 @@ int gmp_server_create(gmp_server** out, int device, const gmp_server_opts* opts)
     co.max_block_out = o.max_block_out;
     co.warps_per_cta = o.warps_per_cta;
     co.max_files = o.max_batch;
+    co.concurrent = 1;  // the lanes' batches overlap on the GPU
     rc = gmp_context_create(&L->ctx, device, &co);
     if (rc) break;
     if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -1,6 +1,9 @@
 """GPU batched decoding: many streams of uneven sizes, MRR and DE mixed, in
 one persistent launch and replayed from a CUDA graph; every file byte-exact
-against the oracle and its own status word."""
+against the oracle and its own status word.  Both ways of handing out work
+items: a fixed first block per warp spread over the SMs (the default) and
+the work counter alone (contexts marked concurrent), also with fewer warps
+than blocks and with two launches overlapping on two streams."""
 import numpy as np
 import pytest
 
@@ -98,3 +101,36 @@ def test_batch_alone_equals_in_mix(gmp):
         alone, st1 = _decode_batch(gmp, ctx, [f])
         assert st1[0] == 0 and np.array_equal(alone[0], got)
     ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(0, 0), (1, 1)])
+def test_batch_concurrent_contexts(gmp, shape):
+    # (1, 1): 152 warps for hundreds of blocks, so most blocks come from the
+    # work counter after a warp's first one
+    import torch
+    files = _files(30, seed=5)
+    ctxs = [gmp.Context(max_block_out=256 * KiB, warps_per_cta=shape[0], ctas_per_sm=shape[1], concurrent=c)
+            for c in (False, True)]
+    for c in ctxs:
+        outs, st = _decode_batch(gmp, c, files)
+        assert np.all(st == 0)
+        for (data, _), got in zip(files, outs):
+            assert np.array_equal(got, data)
+    # two launches at once on two streams, one per context
+    ds = [gmp.DeviceStream(s) for _, s in files]
+    res = []
+    streams = [torch.cuda.Stream() for _ in ctxs]
+    for c, cs in zip(ctxs, streams):
+        outs = [torch.zeros(max(d.orig_size, 1), dtype=torch.uint8, device="cuda") for d in ds]
+        table = gmp.make_file_table([d.file_desc(o, d.orig_size) for d, o in zip(ds, outs)])
+        status = torch.full((len(ds),), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        c.decompress_batch(table, len(ds), status, cs)
+        res.append((outs, status, table))
+    torch.cuda.synchronize()
+    for outs, status, _ in res:
+        assert np.all(status.cpu().numpy() == 0)
+        for (data, _), o, d in zip(files, outs, ds):
+            assert np.array_equal(o[:d.orig_size].cpu().numpy(), data)
+    for c in ctxs:
+        c.close()
