@@ -178,3 +178,29 @@ def test_decode_calls_fail_loudly_without_gpu(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         gmp.Context()
+
+
+@pytest.mark.parametrize("name,cls,expect", [
+    ("gmp_context_opts_default", "ContextOpts",
+     dict(max_block_out=256 << 10, warps_per_cta=0, ctas_per_sm=0, collect_stats=0, max_files=65536, resolve=0,
+          concurrent=0)),
+    ("gmp_server_opts_default", "ServerOpts", None),
+    ("gmp_compress_opts_default", "CompressOpts", None),
+])
+def test_option_structs_match_the_binding(lib, name, cls, expect):
+    # the C default-setter writes every field of the binding's struct (each
+    # starts as a 0xAB pattern) and nothing past its end, so the two layouts
+    # have the same size and fields
+    from paper_1606_00519_gb300 import _native
+    S = getattr(_native, cls)
+    size = ctypes.sizeof(S)
+    buf = (ctypes.c_uint8 * (size + 64))(*([0xAB] * (size + 64)))
+    getattr(lib, name)(ctypes.cast(buf, ctypes.POINTER(S)))
+    assert bytes(buf[size:]) == b"\xab" * 64
+    o = S.from_buffer(buf)
+    for f, t in S._fields_:
+        v = getattr(o, f)
+        pattern = int.from_bytes(b"\xab" * ctypes.sizeof(t), "little")
+        assert v != pattern, f"{cls}.{f} not written by {name}"
+        if expect is not None:
+            assert v == expect[f], (f, v)
