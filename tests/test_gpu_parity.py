@@ -130,6 +130,19 @@ def test_odd_block_sizes_and_small_windows(gmp, ctx):
         check_stream(gmp, ctx, oracle.compress(data[:50_000], p), data[:50_000])
 
 
+@pytest.mark.parametrize("block_size", [256 * KiB, 256 * KiB + 16, 1024 * KiB])
+def test_blocks_of_up_to_1_mib(gmp, block_size):
+    # blocks above the benchmark's 256 KiB: more sequences per block than a
+    # 256 KiB context reserves, sub-blocks of 16 KiB
+    c = gmp.Context(max_block_out=1024 * KiB)
+    data = np.concatenate([datagen.markov_text(1_500_000, seed=21, order=3), datagen.csv_records(1_200_000, seed=22),
+                           np.zeros(300_000, np.uint8)])
+    for de in (False, True):
+        s = gmp.compress(data, block_size, 64, 32 * KiB, de=de)
+        check_stream(gmp, c, s, data)
+    c.close()
+
+
 def test_incompressible_and_degenerate_data(gmp, ctx):
     rng = np.random.default_rng(5)
     rnd = rng.integers(0, 256, 600_000).astype(np.uint8)      # long literal runs (slow path)
