@@ -55,6 +55,15 @@ struct MatchSmem {
   uint8_t ring[kInRing];          // the block's bytes [loaded - kInRing, loaded)
 };
 
+// Bytes x .. x + 3 of the ring (positions taken modulo its size), the first
+// in the low byte: two aligned words and a funnel shift.
+__device__ __forceinline__ uint32_t ring_word(const uint8_t* ring, uint32_t x) {
+  constexpr uint32_t WM = kInRing / 4 - 1;
+  const uint32_t* r = reinterpret_cast<const uint32_t*>(ring);
+  const uint32_t wa = x >> 2;
+  return __funnelshift_r(r[wa & WM], r[(wa + 1) & WM], (x & 3u) * 8u);
+}
+
 __device__ __forceinline__ uint32_t prefix_hash(uint32_t b0, uint32_t b1, uint32_t b2) {
   return ((b0 | (b1 << 8) | (b2 << 16)) * 0x9E3779B1u) >> (32 - kHeadBits);
 }
@@ -104,8 +113,22 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(const uint8_t* in,
           if (d > window) break;  // links run back in position
           // a candidate that differs at the current best length cannot beat it
           if (ml >= lim || M.ring[(cand + ml) & RM] == M.ring[(p + ml) & RM]) {
+            // match length: four bytes per step (the first differing byte
+            // of a word from the XOR's lowest set bit), the last 0..3 bytes
+            // one at a time
             uint32_t k = 0;
-            while (k < lim && M.ring[(cand + k) & RM] == M.ring[(p + k) & RM]) k++;
+            for (;;) {
+              if (k + 4 > lim) {
+                while (k < lim && M.ring[(cand + k) & RM] == M.ring[(p + k) & RM]) k++;
+                break;
+              }
+              const uint32_t x = ring_word(M.ring, cand + k) ^ ring_word(M.ring, p + k);
+              if (x) {
+                k += (uint32_t)(__ffs((int)x) - 1) >> 3;
+                break;
+              }
+              k += 4;
+            }
             if (k >= 3 && k > ml) {
               ml = k;
               dist = d;
