@@ -343,6 +343,16 @@ int gmp_decompress_host_batch(gmp_context* ctx, size_t n_files, const void* cons
 /* One stream: host_out holds out_cap bytes; *status receives the status. */
 int gmp_decompress_host(gmp_context* ctx, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,
                         int32_t* status, void* stream);
+/* The paper's "(In)" mode (Sec. 5.4: compressed input in host memory, the
+   decompressed output left on the GPU): as gmp_decompress_host_batch, but
+   d_outs[f] are device buffers of the context's device (out_caps[f] bytes
+   each), which the pieces decode into directly; there are no copies back.
+   The input copies overlap the decoding of earlier pieces.  Synchronous in
+   the same way (returns with every output in device memory and statuses[f]
+   filled in on the host). */
+int gmp_decompress_from_host_batch(gmp_context* ctx, size_t n_files, const void* const* host_streams,
+                                   const size_t* bytes, void* const* d_outs, const size_t* out_caps, int32_t* statuses,
+                                   void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of decompression requests under a device

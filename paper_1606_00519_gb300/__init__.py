@@ -295,6 +295,25 @@ class Context:
                                                  _stream_handle(cuda_stream)), "gmp_decompress_host_batch")
         return [o[:i.orig_size] for o, i in zip(outs, infos)], [int(x) for x in st]
 
+    def decompress_from_host_batch(self, streams, outs=None, cuda_stream=None):
+        """Host streams in, device bytes out (the paper's "(In)" mode): one
+        pipelined call whose input copies overlap the decoding; outs are uint8
+        CUDA tensors (allocated when None).  Returns (outputs, statuses)."""
+        torch = _torch()
+        ss = [_np_bytes(x) for x in streams]
+        infos = [stream_info(x) for x in ss]
+        if outs is None:
+            outs = [torch.empty(max(i.orig_size, 1), dtype=torch.uint8, device=f"cuda:{self.device}") for i in infos]
+        n = len(ss)
+        ins = (ctypes.c_void_p * n)(*[x.ctypes.data for x in ss])
+        sizes = (ctypes.c_size_t * n)(*[x.size for x in ss])
+        optr = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        caps = (ctypes.c_size_t * n)(*[o.numel() for o in outs])
+        st = (ctypes.c_int32 * n)()
+        _check(self._L.gmp_decompress_from_host_batch(self._h, n, ins, sizes, optr, caps, st,
+                                                      _stream_handle(cuda_stream)), "gmp_decompress_from_host_batch")
+        return [o[:i.orig_size] for o, i in zip(outs, infos)], [int(x) for x in st]
+
     def decompress_host(self, stream, out: np.ndarray | None = None, cuda_stream=None):
         """Host stream in, host bytes out (H2D + decode + D2H, pipelined,
         synchronous)."""

@@ -164,6 +164,7 @@ def _declare(L):
     L.gmp_stats_read.argtypes = [vp, P(Stats)]
     L.gmp_decompress_host.argtypes = [vp, vp, sz, vp, sz, P(ctypes.c_int32), vp]
     L.gmp_decompress_host_batch.argtypes = [vp, sz, vp, vp, vp, vp, vp, vp]
+    L.gmp_decompress_from_host_batch.argtypes = [vp, sz, vp, vp, vp, vp, vp, vp]
     L.gmp_server_opts_default.argtypes = [P(ServerOpts)]
     L.gmp_server_opts_default.restype = None
     L.gmp_server_create.argtypes = [P(vp), i32, P(ServerOpts)]

@@ -467,8 +467,13 @@ int gmp_stats_read(gmp_context* c, gmp_stats* out) {
   return GMP_OK;
 }
 
-int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const* host_streams, const size_t* bytes,
-                              void* const* host_outs, const size_t* out_caps, int32_t* statuses, void* stream) {
+// Host streams in; outputs in host memory (to_device false: decoded into the
+// context's device staging and copied back piece by piece) or in device
+// memory (to_device true: decoded straight into the caller's buffers).
+static int decompress_from_host(gmp_context* c, size_t n_files, const void* const* host_streams, const size_t* bytes,
+                                void* const* outs, const size_t* out_caps, int32_t* statuses, void* stream,
+                                bool to_device) {
+  void* const* host_outs = outs;
   if (!c || (n_files && (!host_streams || !bytes || !host_outs || !out_caps || !statuses))) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -539,7 +544,7 @@ int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const*
   };
   int rc;
   if ((rc = grow(&c->h_comp, &c->h_comp_cap, std::max<uint64_t>(comp_total, 16)))) return rc;
-  if ((rc = grow(&c->h_out, &c->h_out_cap, std::max<uint64_t>(out_total, 16)))) return rc;
+  if (!to_device && (rc = grow(&c->h_out, &c->h_out_cap, std::max<uint64_t>(out_total, 16)))) return rc;
   if ((rc = grow(&c->h_index, &c->h_index_cap, std::max<uint64_t>(n_total, 1) * sizeof(gmp_block_ref)))) return rc;
   if ((rc = grow(&c->h_status, &c->h_status_cap, std::max<size_t>(n_pieces, 1) * sizeof(int32_t)))) return rc;
   for (uint64_t k = 0; k < parts; k++) {
@@ -580,8 +585,9 @@ int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const*
     GMP_CUDA(cudaMemsetAsync(c->h_status + j, 0, sizeof(int32_t), t));
     unsigned long long* counter = c->counter + 48 + k;
     GMP_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), t));
-    gmp_file_desc D{c->h_comp + F.comp_off, bytes[q.file], c->h_index + F.idx_off + q.b0, q.b1 - q.b0,
-                    c->h_out + F.out_off, F.info.orig_size};
+    uint8_t* dec_out = to_device ? static_cast<uint8_t*>(outs[q.file]) : c->h_out + F.out_off;
+    gmp_file_desc D{c->h_comp + F.comp_off, bytes[q.file], c->h_index + F.idx_off + q.b0, q.b1 - q.b0, dec_out,
+                    F.info.orig_size};
     gmp::LaunchShape shape = c->shape;
     shape.grid = (int)std::min<uint64_t>((q.b1 - q.b0 + wpc - 1) / wpc, part_warps / wpc);
     GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &D, c->h_status + j, counter,
@@ -599,7 +605,7 @@ int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const*
     const uint64_t o1 = F.idx[q.b1 - 1].out_offset + F.idx[q.b1 - 1].out_bytes;
     cudaStream_t u = c->d2h[j % parts];
     GMP_CUDA(cudaStreamWaitEvent(u, c->events[2 * j + 1], 0));
-    if (o1 > o0)
+    if (o1 > o0 && !to_device)
       GMP_CUDA(cudaMemcpyAsync(static_cast<uint8_t*>(host_outs[q.file]) + o0, c->h_out + F.out_off + o0, o1 - o0,
                                cudaMemcpyDeviceToHost, u));
   }
@@ -619,6 +625,17 @@ int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const*
   for (size_t j = 0; j < n_pieces; j++)
     if (st[j] && !statuses[pieces[j].file]) statuses[pieces[j].file] = st[j];
   return GMP_OK;
+}
+
+int gmp_decompress_host_batch(gmp_context* c, size_t n_files, const void* const* host_streams, const size_t* bytes,
+                              void* const* host_outs, const size_t* out_caps, int32_t* statuses, void* stream) {
+  return decompress_from_host(c, n_files, host_streams, bytes, host_outs, out_caps, statuses, stream, false);
+}
+
+int gmp_decompress_from_host_batch(gmp_context* c, size_t n_files, const void* const* host_streams,
+                                   const size_t* bytes, void* const* d_outs, const size_t* out_caps, int32_t* statuses,
+                                   void* stream) {
+  return decompress_from_host(c, n_files, host_streams, bytes, d_outs, out_caps, statuses, stream, true);
 }
 
 int gmp_decompress_host(gmp_context* c, const void* host_stream, size_t bytes, void* host_out, size_t out_cap,

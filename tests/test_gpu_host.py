@@ -153,3 +153,32 @@ def test_pinned_buffers_edge_cases(gmp):
                                           [_pinned(torch, datas[0].size), _pinned(torch, datas[4].size)])
     assert sts == [0, oracle.BAD_HEADER] and np.array_equal(outs[0], datas[0])
     ctx.close()
+
+
+def test_from_host_to_device_outputs(gmp):
+    # the paper's "(In)" mode: host streams in, outputs left in device memory
+    import torch
+    datas = [datagen.make_data("csv" if i % 2 else "text3", 500_000 + 77_777 * i, 60 + i) for i in range(5)]
+    streams = [gmp.compress(d, 128 * KiB, 32, 32 * KiB, de=(i % 2 == 0), byte_mode=(i == 3))
+               for i, d in enumerate(datas)]
+    for shape in ((0, 0), (1, 1)):  # default shape, and many pieces per partition
+        ctx = gmp.Context(max_block_out=128 * KiB, warps_per_cta=shape[0], ctas_per_sm=shape[1])
+        for pinned in (False, True):
+            ins = [_pin_copy(torch, s) for s in streams] if pinned else streams
+            outs, sts = ctx.decompress_from_host_batch(ins)
+            assert sts == [0] * len(datas)
+            for o, d in zip(outs, datas):
+                assert o.is_cuda and np.array_equal(o.cpu().numpy(), d)
+        ctx.close()
+    # per-file status, and a device buffer that is too small
+    bad = oracle.compress(datas[0], oracle.params(64 * KiB, 16, 8 * KiB))
+    bo = int(bad[64 + 8:72 + 8].view(np.uint64)[0])
+    bad[bo + 8 + ord("e") // 2] ^= 0x0F if ord("e") % 2 == 0 else 0xF0  # block 1's code lengths break Kraft
+    assert oracle.decompress_status(bad) == oracle.BAD_HEADER
+    ctx = gmp.Context(max_block_out=128 * KiB)
+    outs, sts = ctx.decompress_from_host_batch([streams[1], bad])
+    assert sts == [0, oracle.BAD_HEADER] and np.array_equal(outs[0].cpu().numpy(), datas[1])
+    small = torch.empty(datas[1].size - 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gmp.GmpError):
+        ctx.decompress_from_host_batch([streams[1]], [small])
+    ctx.close()
