@@ -180,6 +180,20 @@ def test_decode_calls_fail_loudly_without_gpu(lib):
         gmp.Context()
 
 
+def test_entry_points_reject_null_arguments(lib):
+    # argument checks come before any CUDA call, so they hold on a machine
+    # without a GPU: a null context or null buffers give GMP_ERR_INVALID_ARG
+    INVALID = -1
+    z = ctypes.c_size_t(0)
+    assert lib.gmp_decompress(None, None, 0, None, 0, None, 0, None, None) == INVALID
+    assert lib.gmp_decompress_batch(None, None, 1, None, None) == INVALID
+    assert lib.gmp_decompress_host_batch(None, 1, None, None, None, None, None, None) == INVALID
+    assert lib.gmp_decompress_from_host_batch(None, 1, None, None, None, None, None, None) == INVALID
+    assert lib.gmp_decompress_host(None, None, 0, None, 0, None, None) == INVALID
+    assert lib.gmp_stats_reset(None, None) == INVALID
+    assert lib.gmp_index_build(None, 0, None, 0, ctypes.byref(z), None) == INVALID
+
+
 @pytest.mark.parametrize("name,cls,expect", [
     ("gmp_context_opts_default", "ContextOpts",
      dict(max_block_out=256 << 10, warps_per_cta=0, ctas_per_sm=0, collect_stats=0, max_files=65536, resolve=0,
