@@ -2,11 +2,13 @@
 // arXiv:1606.00519).
 //
 // One persistent launch; each warp repeatedly takes a work item (one block of
-// one stream) from a device counter and decodes it in two phases:
+// one stream; the first one fixed per warp, the rest from a device counter)
+// and decodes it in two phases:
 //
 //  Phase A, Huffman decoding (Sec. 3.2.1): the warp builds the lookup
-//  tables of the block's two canonical trees in shared memory (2048 and 1024
-//  entries; the rare longer codes are decoded from the canonical arrays),
+//  tables of the block's two canonical trees in shared memory (4096 or 2048
+//  literal/length entries, by kernel instance, and 1024 offset entries; the
+//  rare longer codes are decoded from the canonical arrays),
 //  then lane j decodes sub-block j (lanes take j, j+32 for K > 32), starting
 //  at the bit offset given by the prefix sum of the stored sub-block sizes.
 //  One table lookup per symbol, no tree walk.  Each lane writes its
