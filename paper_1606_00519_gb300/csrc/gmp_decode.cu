@@ -713,7 +713,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
                 buf |= (uint64_t)next_word() << nb;
                 nb += 32;
               }
-                uint32_t e2 = S.u.a.off[buf & (OFF_SIZE - 1)];
+              uint32_t e2 = S.u.a.off[buf & (OFF_SIZE - 1)];
               if (e2 == LONG_CODE)
                 e2 = decode_long<OFF_BITS>(S.u.a.coff, S.u.a.sorted_off, (uint32_t)buf & (LUT_SIZE - 1));
               const uint32_t L2 = e2 >> 9, os = e2 & 31u;
@@ -767,7 +767,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
                 buf |= (uint64_t)next_word() << nb;
                 nb += 32;
               }
-                uint32_t e2 = S.u.a.off[buf & (OFF_SIZE - 1)];
+              uint32_t e2 = S.u.a.off[buf & (OFF_SIZE - 1)];
               if (e2 == LONG_CODE)
                 e2 = decode_long<OFF_BITS>(S.u.a.coff, S.u.a.sorted_off, (uint32_t)buf & (LUT_SIZE - 1));
               const uint32_t L2 = e2 >> 9, os = e2 & 31u;
