@@ -77,7 +77,8 @@ def _threads() -> int:
 def markov_text(n: int, seed: int, order: int = 2, lam: float | None = None,
                 rho: float | None = None) -> np.ndarray:
     """n bytes of order-`order` byte Markov text (English-like letters, ~18 %
-    spaces, 1.5 % noise over all byte values)."""
+    spaces, a 1.5 % noise floor that the 4096-entry sampling table turns into
+    about 1-2 % of bytes outside letters and punctuation)."""
     if lam is None:
         lam = TEXT_LAMBDA[order]
     if rho is None:

@@ -40,7 +40,8 @@ static inline double unif(uint64_t r) { return (double)(r >> 11) * (1.0 / 900719
 /* ------------------------------------------------------------------------ */
 /* English-like unigram: a generic public letter-frequency table (percent of
  * letters), space at about 18 % of all characters, a little punctuation and a
- * newline, and a floor of noise spread over all 256 byte values.             */
+ * newline, and a floor of noise spread over all 256 byte values (the 4096-
+ * entry inverse CDF below keeps the values whose mass reaches its steps).    */
 static const char  kLetters[] = "etaoinshrdlcumwfgypbvkjxqz";
 static const double kLetterPct[26] = {12.7, 9.1, 8.2, 7.5, 7.0, 6.7, 6.3, 6.1, 6.0, 4.3, 4.0, 2.8, 2.8,
                                       2.4, 2.4, 2.2, 2.0, 2.0, 1.9, 1.5, 1.0, 0.8, 0.15, 0.15, 0.1, 0.07};
