@@ -406,22 +406,25 @@ void gmp_server_destroy(gmp_server* s);
 /* ------------------------------------------------------------------------ */
 /* Decompression without any device allocation.  The paper has no
    counterpart; this is an interface for callers that cannot call cudaMalloc:
-   code running while a CUDA graph is being captured, host callbacks where the
-   CUDA allocator must not be re-entered, and applications whose memory
-   manager owns the whole device.  gmp_decompress needs a context, whose
-   creation allocates scratch; this call instead uses a scratch area held in
-   a fixed-size __device__ array of the library (about 53 MB on every GPU that
-   loads the library, kept until the process exits).
+   host callbacks and other code where the CUDA allocator must not be
+   re-entered, and applications whose memory manager owns the whole device
+   and forbids allocations by libraries.  gmp_decompress needs a context,
+   whose creation allocates scratch; this call instead uses a scratch area
+   held in a fixed-size __device__ array of the library (about 53 MB on every
+   GPU that loads the library, kept until the process exits).
    Same arguments as gmp_decompress, without a context, plus max_block_out:
    the largest block output of the stream (gmp_stream_info.max_block_out or
    block_size).  Limits: blocks of at most 256 KiB of output (larger:
    GMP_ERR_CAPACITY, and a block found larger on the device sets
-   GMP_STATUS_CAPACITY), decoded by 32 warps at a time.  The first call on a
-   device looks up the array's device address (cudaGetSymbolAddress, which
-   loads the module on that device); make that first call before any stream
-   capture.  Every call shares the one array and clears its work counter:
-   calls whose work overlaps on the GPU (different streams, or the same
-   array from several threads) race and must be serialised by the caller.
+   GMP_STATUS_CAPACITY), decoded by 32 warps at a time.
+   Set-up: the array's device address belongs to one CUDA context.  The
+   first call in each context (on each device, and again after a
+   cudaDeviceReset) looks it up with cudaGetSymbolAddress, which loads the
+   module on that device; later calls in that context reuse it.  Make that
+   first call before any stream capture.
+   Every call shares the one array and clears its work counter: calls whose
+   work overlaps on the GPU (different streams, or several host threads)
+   race and must be serialised by the caller.
    Allocates nothing, neither with cudaMalloc nor through any library. */
 int gmp_decompress_noalloc(const uint8_t* d_comp, size_t comp_bytes, const gmp_block_ref* d_index,
                            size_t n_blocks, uint32_t max_block_out, uint8_t* d_out, size_t out_cap,
@@ -431,6 +434,14 @@ void gmp_noalloc_limits(uint32_t* max_block_out, uint32_t* warps, uint64_t* scra
 
 /* Last CUDA error string of this thread (for GMP_ERR_CUDA). */
 const char* gmp_last_cuda_error(void);
+
+/* The architecture the library's decode kernel was compiled for, as the CUDA
+   runtime reports it on the current device (cudaFuncGetAttributes):
+   binary_version = 10 * major + minor of the kernel's machine code (103 for
+   sm_103a), ptx_version likewise for the virtual architecture it was
+   compiled from.  Either pointer may be NULL.  Needs a GPU: GMP_ERR_CUDA
+   when the runtime has no usable device or no code for it. */
+int gmp_kernel_arch(int* binary_version, int* ptx_version);
 
 #ifdef __cplusplus
 }

@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline / reference leg may import this package.  The product
 library (``paper_1606_00519_gb300``) never imports, links or calls it, and the
-two share no code: only the stream format (documented in ``gmp_oracle.c``'s
-header and in DESIGN.md) is common.
+two share no code: only the stream format (documented field by field in
+``gmp_oracle.c``'s header) is common.
 
 The arithmetic lives in ``gmp_oracle.c`` (plain serial C, each function citing
 the paper's section it follows), compiled with gcc on first use into
@@ -72,7 +72,7 @@ class Report(ctypes.Structure):
                 ("lit_bytes", ctypes.c_uint64), ("match_bytes", ctypes.c_uint64),
                 ("kraft_ok", ctypes.c_int32), ("lengths_ok", ctypes.c_int32), ("offsets_ok", ctypes.c_int32),
                 ("blocks_ok", ctypes.c_int32), ("subblocks_ok", ctypes.c_int32),
-                ("de_strong_ok", ctypes.c_int32), ("de_weak_ok", ctypes.c_int32), ("mrr_ok", ctypes.c_int32),
+                ("de_weak_ok", ctypes.c_int32), ("mrr_ok", ctypes.c_int32),
                 ("groups", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("max_rounds", ctypes.c_uint64),
                 ("copies", ctypes.c_uint64), ("round_hist", ctypes.c_uint64 * 34),
                 ("first_error", ctypes.c_int32), ("subblocks_even", ctypes.c_int32)]

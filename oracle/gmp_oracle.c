@@ -25,14 +25,18 @@
  *     bounds, the DE invariant of Sec. 4.2) and a simulator of Multi-Round
  *     Resolution (Fig. 5, Sec. 4.1) that counts rounds per 32-sequence group.
  *
- * Readings where the paper is silent or garbled (each listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - MRR's HWM is the write position of the lowest-numbered pending lane
  *     (all lanes before it are complete and its literals are written), and a
  *     lane can copy once min(read_pos + length, write_pos) <= HWM, which also
  *     admits overlapping copies (offset < length).  The printed
  *     count_leading_zero_bits / read_pos + length rule is not used as is.
- *   - The DE compressor accepts a match only if its whole source lies below
- *     warpHWM, shortening it to warpHWM - src when that leaves >= 3 bytes.
+ *   - DE (Fig. 7, Sec. 4.2): read literally, a block's first group never
+ *     gets a match (warpHWM = 0 until 32 matches close the group).  The DE
+ *     compressor here lets a match read every byte the one-pass decoder has
+ *     finished before a group's copies run: the bytes below warpHWM and the
+ *     group's literal strings, but no byte an earlier back-reference of the
+ *     same group writes (the candidate is cut at the first such byte).
  *   - A back-reference stores its distance (current position - source).
  *   - Sub-blocks: the block's n_seq sequences are cut into K runs of
  *     ceil(n_seq / K) sequences; trailing runs may be shorter or empty.
@@ -969,7 +973,7 @@ static int mrr_block(const seqbuf* S, uint32_t out_bytes, int de_single_pass, co
 /* Validation report over a whole stream. */
 typedef struct {
   uint64_t n_blocks, n_seq, n_matches, lit_bytes, match_bytes;
-  int32_t kraft_ok, lengths_ok, offsets_ok, blocks_ok, subblocks_ok, de_strong_ok, de_weak_ok, mrr_ok;
+  int32_t kraft_ok, lengths_ok, offsets_ok, blocks_ok, subblocks_ok, de_weak_ok, mrr_ok;
   uint64_t groups, rounds, max_rounds, copies;
   uint64_t round_hist[34];
   int32_t first_error;
@@ -979,7 +983,7 @@ typedef struct {
 int orc_validate(const uint8_t* s, uint64_t len, orc_report* R) {
   memset(R, 0, sizeof(*R));
   R->kraft_ok = R->lengths_ok = R->offsets_ok = R->blocks_ok = R->subblocks_ok = 1;
-  R->de_strong_ok = R->de_weak_ok = R->mrr_ok = 1;
+  R->de_weak_ok = R->mrr_ok = 1;
   R->subblocks_even = 1;
   orc_info I;
   int rc = orc_stream_info(s, len, &I);
@@ -1029,10 +1033,9 @@ int orc_validate(const uint8_t* s, uint64_t len, orc_report* R) {
     }
     uint64_t expect = b + 1 < I.n_blocks ? I.block_size : I.orig_size - b * (uint64_t)I.block_size;
     if (ob != expect) R->blocks_ok = 0;
-    /* window / block bounds and the DE invariant per 32-sequence group */
-    uint64_t p = 0, G0 = 0;
+    /* window and block bounds of every back-reference */
+    uint64_t p = 0;
     for (size_t i = 0; i < S.n; i++) {
-      if (i % 32 == 0) G0 = p;
       p += S.lit_len[i];
       R->lit_bytes += S.lit_len[i];
       if (S.mlen[i]) {
@@ -1040,7 +1043,6 @@ int orc_validate(const uint8_t* s, uint64_t len, orc_report* R) {
         R->match_bytes += S.mlen[i];
         uint32_t d = S.off[i];
         if (d < 1 || d > I.window || d > p) R->offsets_ok = 0;
-        if (p - d + S.mlen[i] > G0) R->de_strong_ok = 0;
       }
       p += S.mlen[i];
     }

@@ -182,6 +182,7 @@ def _declare(L):
     L.gmp_decompress_noalloc.argtypes = [vp, sz, vp, sz, ctypes.c_uint32, vp, sz, vp, vp]
     L.gmp_noalloc_limits.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint64)]
     L.gmp_noalloc_limits.restype = None
+    L.gmp_kernel_arch.argtypes = [P(ctypes.c_int), P(ctypes.c_int)]
     L.gmp_last_cuda_error.argtypes = []
     L.gmp_last_cuda_error.restype = ctypes.c_char_p
 

@@ -1199,8 +1199,16 @@ namespace gmp {
 
 size_t warp_smem_bytes(bool deep) { return deep ? sizeof(WarpSmem<11>) : sizeof(WarpSmem<12>); }
 
+// The dynamic shared memory limit of each kernel instance is set to the
+// largest size any launch shape of that instance uses (16 warps per CTA of
+// the 128-register kernel, 4 of the 96-register one), not to the size of the
+// launch at hand: the attribute is per kernel and process-wide, so a smaller
+// value set by one host thread could otherwise fail another thread's wider
+// launch.  smem_bytes is only checked against that limit.
 cudaError_t configure_kernel(bool deep, size_t smem_bytes) {
-  const int b = (int)smem_bytes;
+  const size_t lim = deep ? 4 * sizeof(WarpSmem<11>) : (size_t)kWideWarpsPerSm * sizeof(WarpSmem<12>);
+  if (smem_bytes > lim) return cudaErrorInvalidValue;
+  const int b = (int)lim;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if (deep) {
@@ -1243,8 +1251,6 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
   P.stats = stats;
   P.collect_stats = collect_stats;
   P.resolve = resolve;
-  // the attribute is per kernel, so set it for this launch's shape (contexts
-  // with different shapes may share the process)
   const bool deep = shape.deep && shape.warps_per_cta <= 4;
   cudaError_t e = configure_kernel(deep, shape.smem_bytes);
   if (e != cudaSuccess) return e;
@@ -1257,6 +1263,15 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
     else decode_kernel<false, false><<<grid, block, shape.smem_bytes, stream>>>(P);
   }
   return cudaGetLastError();
+}
+
+cudaError_t kernel_arch(int* binary_version, int* ptx_version) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, decode_kernel<false, false>);
+  if (e != cudaSuccess) return e;
+  if (binary_version) *binary_version = fa.binaryVersion;
+  if (ptx_version) *ptx_version = fa.ptxVersion;
+  return cudaSuccess;
 }
 
 cudaError_t launch_batch_prefix(const gmp_file_desc* files, uint32_t n_files, uint64_t* item_start,

@@ -92,6 +92,11 @@ extern "C" {
 
 const char* gmp_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
+int gmp_kernel_arch(int* binary_version, int* ptx_version) {
+  const cudaError_t e = gmp::kernel_arch(binary_version, ptx_version);
+  return e == cudaSuccess ? GMP_OK : gmp::cuda_error(e, "cudaFuncGetAttributes");
+}
+
 int gmp_stream_info_parse(const void* host_stream, size_t bytes, gmp_stream_info* info) {
   if (!host_stream || !info) return GMP_ERR_INVALID_ARG;
   const uint8_t* s = static_cast<const uint8_t*>(host_stream);

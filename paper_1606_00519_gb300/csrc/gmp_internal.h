@@ -31,6 +31,8 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
                           unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,
                           uint32_t max_seq, uint32_t max_out, unsigned long long* stats, int collect_stats,
                           int resolve, cudaStream_t stream, int spread = 1);
+// compiled architecture of decode_kernel (cudaFuncGetAttributes)
+cudaError_t kernel_arch(int* binary_version, int* ptx_version);
 cudaError_t launch_batch_prefix(const gmp_file_desc* files, uint32_t n_files, uint64_t* item_start,
                                 cudaStream_t stream);
 

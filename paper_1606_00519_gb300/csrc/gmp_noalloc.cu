@@ -1,21 +1,20 @@
 // gmp_noalloc.cu - decompression of one stream without any device
 // allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (an allocation would break or be recorded into the capture),
-// host callbacks and other contexts where re-entering the CUDA allocator is
-// not allowed, and applications whose memory manager owns the whole device
-// and forbids allocations by libraries.  gmp_decompress needs a context, and
-// creating one allocates its scratch.  This entry point instead uses a
-// scratch area that lives in a file-scope __device__ array of fixed size, so
-// the library loads it with the module and the call itself allocates
-// nothing.  The caller still provides the stream, the block index, the
-// output buffer and the status word.
+// Some callers cannot call cudaMalloc: host callbacks and other code where
+// re-entering the CUDA allocator is not allowed, and applications whose
+// memory manager owns the whole device and forbids allocations by
+// libraries.  gmp_decompress needs a context, and creating one allocates its
+// scratch.  This entry point instead uses a scratch area that lives in a
+// file-scope __device__ array of fixed size, so the library loads it with the
+// module and the call itself allocates nothing.  The caller still provides
+// the stream, the block index, the output buffer and the status word.
 //
 // Limits: blocks of at most kMaxBlockOut (256 KiB) of output, decoded by
 // kSlots (32) warps at a time.  The array holds one scratch slot per warp plus
 // a header with the work counter; every GPU that loads this library keeps
 // about 53 MB of it until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,35 +35,75 @@ constexpr uint64_t kShadowBytes = (uint64_t)kMaxBlockOut + 16ull * gmp::kMaxSub 
 constexpr uint64_t kSlotBytes = (kRecBytes + kShadowBytes + 255) & ~uint64_t(255);
 constexpr uint64_t kHeaderBytes = 256;  // work counter and statistics words
 constexpr uint64_t kScratchBytes = kHeaderBytes + kSlotBytes * kSlots;
-constexpr int kMaxDevices = 64;
-
+// device addresses of the scratch, one per CUDA context that has called
+// (a context's id is never reused within the process, unlike its handle)
+constexpr int kMaxContexts = 64;
+struct CtxAddr {
+  unsigned long long ctx_id;
+  uint8_t* addr;
+};
 std::mutex g_mu;
-uint8_t* g_addr[kMaxDevices] = {};
+CtxAddr g_addr[kMaxContexts] = {};
+int g_n_addr = 0;
 
 }  // namespace
 
 // The scratch of gmp_decompress_noalloc.  In host code this name is only a
 // stand-in for the device object; kernels receive the device address that
-// cudaGetSymbolAddress returns for the current device.
+// cudaGetSymbolAddress returns in the current context.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
-// Device address of the scratch on the current device, looked up once per
-// device (the lookup loads this file's module on that device).
-int scratch_address(uint8_t** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return GMP_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return GMP_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> g(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return GMP_ERR_CUDA;
-    g_addr[dev] = static_cast<uint8_t*>(p);
+// Id of the calling thread's current CUDA context; false if there is none.
+// The two driver calls are fetched through the runtime, so the library does
+// not link the driver library itself.  Called with g_mu held.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return false;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
   }
-  *out = g_addr[dev];
+  CUcontext c = nullptr;
+  return get_current(&c) == CUDA_SUCCESS && c && get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch in the current context.  The address is the
+// array's instance in one context: a context made after cudaDeviceReset, or
+// another context current on the same device, has its own.  So the set-up
+// (cudaGetSymbolAddress, which also loads this file's module and makes the
+// device's primary context current if no context is) runs once per context,
+// keyed by the context's id, and later calls look the address up.
+int scratch_address(uint8_t** out) {
+  unsigned long long id = 0;
+  std::lock_guard<std::mutex> g(g_mu);
+  if (current_context_id(&id)) {
+    for (int i = 0; i < g_n_addr; i++)
+      if (g_addr[i].ctx_id == id) {
+        *out = g_addr[i].addr;
+        return GMP_OK;
+      }
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) return gmp::cuda_error(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                     "cudaGetSymbolAddress");
+  if (!current_context_id(&id)) return GMP_ERR_CUDA;
+  // a full table starts over (only a process that cycles through more than
+  // kMaxContexts contexts gets here)
+  if (g_n_addr == kMaxContexts) g_n_addr = 0;
+  g_addr[g_n_addr++] = CtxAddr{id, static_cast<uint8_t*>(p)};
+  *out = static_cast<uint8_t*>(p);
   return GMP_OK;
 }
 

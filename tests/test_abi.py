@@ -36,9 +36,17 @@ def test_library_exports_every_declared_function(lib):
     assert not missing, missing
 
 
-def test_library_is_built_for_sm103a_only():
-    from paper_1606_00519_gb300 import _native
-    assert _native.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+@pytest.mark.gpu
+def test_decode_kernel_is_compiled_for_sm103(lib):
+    """The runtime's own report of the loaded kernel's code: machine code and
+    virtual architecture both 10.3 (a library built for another arch would
+    report that arch, or fail to load the kernel at all)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    b, p = ctypes.c_int(), ctypes.c_int()
+    assert lib.gmp_kernel_arch(ctypes.byref(b), ctypes.byref(p)) == 0, lib.gmp_last_cuda_error()
+    assert b.value == 103 and p.value == 103, (b.value, p.value)
 
 
 def test_compressor_streams_validate_and_roundtrip(lib):

@@ -1,13 +1,14 @@
 """gmp_decompress_noalloc through the C ABI, against the context path.
 
-Callers that cannot call cudaMalloc (a CUDA graph capture in progress, host
-callbacks that must not re-enter the allocator, applications whose memory
-manager owns the device) use gmp_decompress_noalloc, which decodes with a
-fixed scratch array inside the library instead of a context's allocation.
-Its output must equal gmp_decompress's byte for byte (the tolerance of every
-decoder test here), call after call, since every call reuses the same array.
-The file name sorts last so that a run stopping at the first failure has
-already run every other test."""
+Callers that cannot call cudaMalloc (host callbacks that must not re-enter
+the allocator, applications whose memory manager owns the device) use
+gmp_decompress_noalloc, which decodes with a fixed scratch array inside the
+library instead of a context's allocation.  Its output must equal
+gmp_decompress's byte for byte (the tolerance of every decoder test here),
+call after call, since every call reuses the same array; and the calls after
+the first in a context (which looks up the array's address) must leave the
+device's free memory unchanged.  The file name sorts last so that a run
+stopping at the first failure has already run every other test."""
 import ctypes
 
 import numpy as np
@@ -50,13 +51,21 @@ def test_noalloc_equals_context_path_on_consecutive_calls(env, mode):
     ctx = gmp.Context(max_block_out=w.block_size)
     ref, st = ctx.decompress(ds)
     assert st == 0 and np.array_equal(ref.cpu().numpy(), data)
+    outs = [torch.full((data.size,), 0x33, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    statuses = [torch.full((1,), -1, dtype=torch.int32, device="cuda") for _ in range(2)]
+    # the first call in this context may look up the array's address
+    assert _noalloc(L, torch, ds, outs[0], statuses[0], ds.info.max_block_out) == 0
+    torch.cuda.synchronize()
     for call in range(2):
-        out = torch.full((data.size,), 0x33, dtype=torch.uint8, device="cuda")
-        status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
-        assert _noalloc(L, torch, ds, out, status, ds.info.max_block_out) == 0
+        outs[call].fill_(0x33)
+        statuses[call].fill_(-1)
         torch.cuda.synchronize()
-        assert int(status.item()) == 0, call
-        assert torch.equal(out, ref), call
+        free_before = torch.cuda.mem_get_info()[0]
+        assert _noalloc(L, torch, ds, outs[call], statuses[call], ds.info.max_block_out) == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free_before, call
+        assert int(statuses[call].item()) == 0, call
+        assert torch.equal(outs[call], ref), call
     ctx.close()
 
 
