@@ -4,9 +4,17 @@
 One step = one pass of the whole decode path over the workload: Huffman
 decoding of every sub-block, then LZ77 resolution of every block, for the
 workload's MRR stream and its DE stream, in one persistent launch of the
-batched decoder.  Inputs (compressed streams and block indexes) are resident
-in device memory before the timed region; the decompressed output (2 x 256 MiB
-for the default workload) is larger than L2, so no flush is needed.
+batched decoder.  The default workload is the 1 GiB configuration: CSV-like
+numeric records (csv1g), 256 KiB blocks of 32 sub-blocks, compressed once in
+MRR and once in DE mode.  Inputs (compressed streams and block indexes) are
+resident in device memory before the timed region; the decompressed output
+(2 x 1 GiB) is larger than L2, so no flush is needed.
+
+The same JSON line carries, for one GPU, sub-objects for the other
+configurations: ``text256m`` (256 MiB Markov text, MRR + DE), ``batch_1gib``
+(the seeded 1 GiB cut of the 4096-file mix in one CUDA-graph launch, against
+one launch per file) and ``serving`` (Poisson arrivals under a 32 GiB budget:
+closed-loop peak, p50/p99 at 25/50/90 % of it, against one call per request).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
 slow, obviously correct serial decoder) on a bounded sample instead.
@@ -50,11 +58,11 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic_per_unit(fmt: str = "bit"):
+def _traffic_per_unit(fmt: str = "bit", workload: str = "csv1g"):
     """DRAM bytes per decompressed byte of the decode kernel from the committed
-    ncu summary of the stream format, if it was taken on the current kernel
-    source."""
-    name = "decode_kernel_traffic.json" if fmt == "bit" else f"decode_kernel_traffic_{fmt}.json"
+    ncu summary of the workload and stream format, if it was taken on the
+    current kernel source."""
+    name = f"decode_kernel_traffic_{workload}" + ("" if fmt == "bit" else f"_{fmt}") + ".json"
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
@@ -72,7 +80,7 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int, period_ms: int = 50):
+    def __init__(self, gpu_index: int, period_ms: int = 20):
         self.proc = None
         # raw samples (the JSON line carries their summary)
         out_dir = os.environ.get("GMP_CLOCKS_DIR") or tempfile.gettempdir()
@@ -233,14 +241,56 @@ def cpu_oracle_parallel(streams, budget_s: float, threads: int, max_blocks: int 
     return state["bytes"], el, desc
 
 
+def _oracle_pool(w, fmt: str, pool_bytes: int, threads: int):
+    """Streams for the reference arm, written by the oracle's own compressor
+    (no product code on that path): the first pool_bytes of the workload in
+    chunks of whole blocks, each chunk compressed as its own stream on a host
+    thread (blocks are independent, Sec. 3.1, so the chunks' blocks are the
+    blocks of one stream of the whole).  Returns {mode: [stream, ...]}."""
+    import threading
+
+    import oracle
+    data = w.data(min(w.size, pool_bytes))
+    chunk = max(w.block_size, (data.size // (4 * threads)) // w.block_size * w.block_size)
+    pieces = [data[i:i + chunk] for i in range(0, data.size, chunk)]
+    pool = {}
+    for mode in ("mrr", "de"):
+        prm = oracle.params(w.block_size, w.n_sub if fmt == "bit" else 1, w.window, de=(mode == "de"),
+                            byte_mode=(fmt == "byte"))
+        out = [None] * len(pieces)
+        nxt = [0]
+        lock = threading.Lock()
+
+        def work():
+            while True:
+                with lock:
+                    k = nxt[0]
+                    nxt[0] += 1
+                if k >= len(pieces):
+                    return
+                out[k] = oracle.compress(pieces[k], prm)
+
+        ts = [threading.Thread(target=work) for _ in range(threads)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        pool[mode] = out
+    return pool, data.size
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle's serial block decoder, run
+    block-parallel on all host cores, on a bounded sample of the workload per
+    step (args.ref_blocks blocks per thread)."""
     rank, world, local, dist = _dist_init(args)
     if rank != 0:
         return
-    w, data, streams = make_workload(args.workload, args.size, args.format)
-    # each step decodes a bounded sample (the serial oracle is slow),
-    # block-parallel on all host cores
+    import oracle
+    w = datagen.WORKLOADS[args.workload]
     threads = os.cpu_count() or 1
+    pool, pool_bytes = _oracle_pool(w, args.format, args.ref_pool, threads)
+    streams = {f"{m}{i}": st for m in pool for i, st in enumerate(pool[m])}
     per_step_blocks = args.ref_blocks * threads
     for _ in range(args.warmup):
         cpu_oracle_parallel(streams, 1e9, threads, max_blocks=threads)
@@ -250,38 +300,42 @@ def run_reference(args):
         tot_b += nb
         tot_t += el
     gbs = tot_b / tot_t / 1e9
+    comp = sum(st.size for m in pool for st in pool[m])
+    sample = (f"per step: {per_step_blocks} blocks ({per_step_blocks * w.block_size} bytes) of a pool of the first "
+              f"{pool_bytes} bytes of the workload compressed by the oracle in MRR and DE mode (ratio "
+              f"{2 * pool_bytes / comp:.3f}), block-parallel on {threads} threads")
     line = {"impl": "reference", "metric": "decompressed GB/s", "value": gbs, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": _config(w, streams, data, args.format),
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle",
-                             "sample": f"per step: {desc}"},
+            "data": "synthetic", "config": _config(w, args.format, world, args.size),
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _config(w, streams, data, fmt="bit"):
+def _config(w, fmt="bit", world=1, size=None):
+    """The workload as both arms describe it (the same keys and values)."""
+    size = int(size or w.size)
     if fmt == "byte":
         coding = "Gompresso/Byte (byte-level records, no Huffman)"
     else:
         coding = f"K={w.n_sub} sub-blocks"
-    return {"workload": f"{w.name}: {w.size // MiB} MiB {w.kind}, {w.block_size // KiB} KiB blocks, "
+    return {"workload": f"{w.name}: {size / MiB:g} MiB {w.kind}, {w.block_size // KiB} KiB blocks, "
                         f"{coding}, {w.window // KiB} KiB window, MRR and DE streams",
-            "format": fmt, "bytes_per_stream": int(data.size), "block_size": w.block_size,
+            "format": fmt, "bytes_per_stream": size, "block_size": w.block_size,
             "n_sub": w.n_sub if fmt == "bit" else 0, "window": w.window, "cwl": 12 if fmt == "bit" else 0,
-            "ratio_mrr": round(data.size / streams["mrr"].size, 4),
-            "ratio_de": round(data.size / streams["de"].size, 4),
-            "l2": "inputs larger than L2 (no flush)"}
+            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"}
 
 
-def run_gmp(args):
+def measure_decode(args, w, data, streams, dev, dist=None, rank=0, clocks=False, extras=True):
+    """Times `args.steps` batched launches decoding the workload's MRR and DE
+    streams (one launch per step) after a byte-exact check; returns the
+    figures of the JSON line.  extras: per-stream rates and the statistics
+    launch with the cycle split of the decode kernel."""
     import torch
     import paper_1606_00519_gb300 as gmp
 
-    rank, world, local, dist = _dist_init(args)
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w, data, streams = make_workload(args.workload, args.size, args.format)
+    local = dev.index or 0
     modes = ["mrr", "de"]
     ds = {m: gmp.DeviceStream(streams[m], device=dev) for m in modes}
     outs = {m: torch.empty(data.size, dtype=torch.uint8, device=dev) for m in modes}
@@ -296,7 +350,7 @@ def run_gmp(args):
     if not args.warps_per_cta:
         tuned = ctx.autotune(table, len(modes), status, stream)
     shape = {"warps_per_cta": tuned["warps_per_cta"] if tuned else args.warps_per_cta,
-             "ctas_per_sm": tuned["ctas_per_sm"] if tuned else 0}
+             "ctas_per_sm": tuned["ctas_per_sm"] if tuned else 0, "autotuned": tuned is not None}
     out_bytes = data.size * len(modes)
     comp_bytes = sum(ds[m].comp_bytes for m in modes)
 
@@ -304,6 +358,8 @@ def run_gmp(args):
         ctx.decompress_batch(table, len(modes), status, stream)
 
     # correctness of the timed configuration (byte-exact against the input)
+    for o in outs.values():
+        o.fill_(0xA5)
     step()
     torch.cuda.synchronize()
     ref = torch.from_numpy(data).to(dev)
@@ -311,71 +367,111 @@ def run_gmp(args):
     ok = bool(np.all(st == 0)) and all(bool(torch.equal(outs[m], ref)) for m in modes)
     del ref
     if not ok:
-        raise SystemExit(f"bench: decoded output is not byte-exact (status {st.tolist()})")
+        raise SystemExit(f"bench: {w.name} decoded output is not byte-exact (status {st.tolist()})")
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local) if rank == 0 else None
+    sampler = ClockSampler(local) if clocks else None
     _barrier(dist)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launch_ms = []
+    launch_ev = []
     ev0.record(stream)
     for _ in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         step()
         b.record(stream)
-        launch_ms.append((a, b))
+        launch_ev.append((a, b))
     ev1.record(stream)
     torch.cuda.synchronize()
     _barrier(dist)
     el_ms = ev0.elapsed_time(ev1)
-    per_launch = [a.elapsed_time(b) for a, b in launch_ms]
-    clk = clocks.stop() if clocks else None
+    per_launch = [a.elapsed_time(b) for a, b in launch_ev]
+    clk = sampler.stop() if sampler else None
     el_ms = _max_over_ranks(dist, el_ms)
     total_bytes = _sum_over_ranks(dist, float(out_bytes * args.steps))
     value = total_bytes / (el_ms / 1e3) / 1e9
 
-    # per-mode throughput (each stream in its own launch), for context
-    per_mode = {}
-    for m in modes:
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        st1 = torch.zeros(1, dtype=torch.int32, device=dev)
-        ctx.decompress_into(ds[m], outs[m], st1, stream)
-        torch.cuda.synchronize()
-        a.record(stream)
-        reps = max(3, args.steps // 2)
-        for _ in range(reps):
+    hbm_peak, peak_kind = _peaks()
+    launch_avg_ms = float(np.mean(per_launch))
+    algo_bytes = comp_bytes + out_bytes  # compressed read + decompressed written
+    achieved = algo_bytes / (launch_avg_ms / 1e3) / 1e9
+    tpu, _ = _traffic_per_unit(args.format, w.name)
+    res = {
+        "value": round(value, 3), "ms_per_step": round(el_ms / args.steps, 4), "unit": "GB/s",
+        "launch_shape": shape,
+        "streams": {"ratio_mrr": round(data.size / streams["mrr"].size, 4),
+                    "ratio_de": round(data.size / streams["de"].size, 4), "compressed_bytes": int(comp_bytes),
+                    "compressor": "gmp_compress (host, lazy parse)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
+                     "traffic": (round(tpu * out_bytes) if tpu else None),
+                     "kernel": "gmp::decode_kernel (persistent; one launch per step)",
+                     "algorithmic_bytes_per_launch": int(algo_bytes),
+                     "launch_avg_ms": round(launch_avg_ms, 4),
+                     "decompressed_frac_of_roofline": round(value / (hbm_peak * (out_bytes / algo_bytes)), 4)},
+        "clocks": clk,
+    }
+    if extras:
+        # per-mode throughput (each stream in its own launch), for context
+        per_mode = {}
+        for m in modes:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st1 = torch.zeros(1, dtype=torch.int32, device=dev)
             ctx.decompress_into(ds[m], outs[m], st1, stream)
-        b.record(stream)
+            torch.cuda.synchronize()
+            a.record(stream)
+            reps = max(3, args.steps // 2)
+            for _ in range(reps):
+                ctx.decompress_into(ds[m], outs[m], st1, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            per_mode[m] = round(data.size * reps / (a.elapsed_time(b) / 1e3) / 1e9, 2)
+        res["per_mode_gbs"] = per_mode
+        # where the decode kernel spends its cycles (one extra launch with the
+        # per-phase clock counters on, outside the timed region)
+        sctx = gmp.Context(device=local, max_block_out=w.block_size, warps_per_cta=shape["warps_per_cta"],
+                           ctas_per_sm=shape["ctas_per_sm"], collect_stats=True)
+        sctx.stats_reset(stream)
+        sctx.decompress_batch(table, len(modes), status, stream)
         torch.cuda.synchronize()
-        per_mode[m] = round(data.size * reps / (a.elapsed_time(b) / 1e3) / 1e9, 2)
+        phase = sctx.stats()
+        sctx.close()
+        cyc = phase["cycles_tables"] + phase["cycles_huffman"] + phase["cycles_lz77"]
+        res["decode_kernel_cycles"] = {
+            "tables": round(phase["cycles_tables"] / max(cyc, 1), 4),
+            "huffman": round(phase["cycles_huffman"] / max(cyc, 1), 4),
+            "lz77": round(phase["cycles_lz77"] / max(cyc, 1), 4),
+            "cycles_per_block": round(cyc / max(phase["blocks"], 1)),
+            "mrr_rounds_per_group": round(phase["rounds"] / max(phase["groups"], 1), 3),
+            "max_rounds": phase["max_rounds"], "de_fallback_groups": phase["de_fallback_groups"]}
+    ctx.close()
+    return res, (ds, outs, comp_bytes, out_bytes)
 
-    # where the decode kernel spends its cycles (one extra launch with the
-    # per-phase clock counters on, outside the timed region)
-    sctx = gmp.Context(device=local, max_block_out=w.block_size, warps_per_cta=shape["warps_per_cta"],
-                       ctas_per_sm=shape["ctas_per_sm"], collect_stats=True)
-    sctx.stats_reset(stream)
-    sctx.decompress_batch(table, len(modes), status, stream)
-    torch.cuda.synchronize()
-    phase = sctx.stats()
-    sctx.close()
-    cyc = phase["cycles_tables"] + phase["cycles_huffman"] + phase["cycles_lz77"]
-    phase_split = {"tables": round(phase["cycles_tables"] / max(cyc, 1), 4),
-                   "huffman": round(phase["cycles_huffman"] / max(cyc, 1), 4),
-                   "lz77": round(phase["cycles_lz77"] / max(cyc, 1), 4),
-                   "cycles_per_block": round(cyc / max(phase["blocks"], 1)),
-                   "mrr_rounds_per_group": round(phase["rounds"] / max(phase["groups"], 1), 3),
-                   "max_rounds": phase["max_rounds"], "de_fallback_groups": phase["de_fallback_groups"]}
+
+def run_gmp(args):
+    import torch
+    import paper_1606_00519_gb300 as gmp
+
+    rank, world, local, dist = _dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, data, streams = make_workload(args.workload, args.size, args.format)
+    res, (ds, outs, comp_bytes, out_bytes) = measure_decode(args, w, data, streams, dev, dist, rank,
+                                                            clocks=(rank == 0))
+    modes = ["mrr", "de"]
+    stream = torch.cuda.current_stream(dev)
 
     # end to end through the public host-to-host call: pinned host input,
     # H2D of the compressed streams, decode, D2H of the decompressed bytes,
     # one pipelined call per step for both streams
+    e2e_ctx = gmp.Context(device=local, max_block_out=w.block_size,
+                          warps_per_cta=res["launch_shape"]["warps_per_cta"],
+                          ctas_per_sm=res["launch_shape"]["ctas_per_sm"])
     pin_in = [torch.from_numpy(streams[m].copy()).pin_memory().numpy() for m in modes]
     pin_out = [torch.empty(data.size, dtype=torch.uint8).pin_memory().numpy() for m in modes]
-    e2e_ctx = ctx
     e2e_ctx.decompress_host_batch(pin_in, pin_out, stream)  # staging allocated outside the timed region
     torch.cuda.synchronize()
     _barrier(dist)
@@ -390,9 +486,13 @@ def run_gmp(args):
     e2e_val = _sum_over_ranks(dist, float(out_bytes * e2e_steps)) / e2e_s / 1e9
     if not all(np.array_equal(o, data) for o in pin_out):
         raise SystemExit("bench: e2e output is not byte-exact")
+    del pin_out
     # the paper's "(In)" mode: the same pinned input, H2D overlapped with the
-    # decode, the output left in device memory
-    dev_out = [torch.empty(data.size, dtype=torch.uint8, device="cuda") for m in modes]
+    # decode, the output left in device memory (the outputs of the timed
+    # launches are reused)
+    dev_out = [outs[m] for m in modes]
+    for o in dev_out:
+        o.fill_(0x5A)
     e2e_ctx.decompress_from_host_batch(pin_in, dev_out, stream)
     torch.cuda.synchronize()
     _barrier(dist)
@@ -404,62 +504,67 @@ def run_gmp(args):
     torch.cuda.synchronize()
     in_s = _max_over_ranks(dist, time.perf_counter() - t0)
     in_val = _sum_over_ranks(dist, float(out_bytes * e2e_steps)) / in_s / 1e9
-    ref_dev = torch.from_numpy(data).cuda()
+    ref_dev = torch.from_numpy(data).to(dev)
     if not all(torch.equal(o, ref_dev) for o in dev_out):
         raise SystemExit("bench: input-only end-to-end output is not byte-exact")
-    del ref_dev, dev_out
+    del ref_dev, dev_out, pin_in
+    e2e_ctx.close()
+    del ds, outs
+    torch.cuda.empty_cache()
 
-    if rank != 0:
-        return
-    hbm_peak, peak_kind = _peaks()
-    launch_avg_ms = float(np.mean(per_launch))
-    algo_bytes = comp_bytes + out_bytes  # compressed read + decompressed written
-    achieved = algo_bytes / (launch_avg_ms / 1e3) / 1e9
-    tpu, tinfo = _traffic_per_unit(args.format)
     line = {
-        "metric": "decompressed GB/s", "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4),
+        "metric": "decompressed GB/s", "value": res["value"], "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {**_config(w, streams, data, args.format), "parallelism": f"replicas x{world}",
-                   "launch_shape": {**shape, "autotuned": tuned is not None}, "per_mode_gbs": per_mode,
-                   "decode_kernel_cycles": phase_split},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
-                     "traffic": (round(tpu * out_bytes) if tpu else None),
-                     "kernel": "gmp::decode_kernel (persistent; one launch per step)",
-                     "algorithmic_bytes_per_launch": int(algo_bytes),
-                     "decompressed_frac_of_roofline": round(
-                         value / (hbm_peak * (out_bytes / algo_bytes)), 4)},
+        "config": _config(w, args.format, world, data.size),
+        "launch_shape": res["launch_shape"], "streams": res["streams"], "per_mode_gbs": res.get("per_mode_gbs"),
+        "decode_kernel_cycles": res.get("decode_kernel_cycles"),
+        "roofline": res["roofline"],
         "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": int(comp_bytes),
                 "d2h_bytes_per_step": int(out_bytes),
                 "input_only": {"value": round(in_val, 3), "unit": "GB/s", "h2d_bytes_per_step": int(comp_bytes),
                                "d2h_bytes_per_step": 0,
                                "call": "decompress_from_host_batch (output left in device memory)"}},
         "gpu_launches": 2 * args.steps,
-        "clocks": clk,
+        "clocks": res["clocks"],
     }
-    if not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         nb, el, desc = cpu_oracle_parallel(streams, args.cpu_budget / 4, threads)
         nb1, el1, desc1 = cpu_oracle_sample(streams, args.cpu_budget * 3 / 4)
         line["cpu_baseline"] = {"value": round(nb / el / 1e9, 5), "unit": "GB/s", "cores": threads,
                                 "kind": "oracle", "sample": desc,
                                 "single_thread": {"value": round(nb1 / el1 / 1e9, 5), "cores": 1, "sample": desc1}}
-    print(json.dumps(line), flush=True)
+    del streams, data
+    # the other configurations, on one GPU (a scaling run reports the main
+    # workload only)
+    if world == 1 and not args.no_extras:
+        tw = datagen.WORKLOADS["text256m"]
+        if args.workload != "text256m":
+            _, tdata, tstreams = make_workload("text256m", None, args.format)
+            tres, bufs = measure_decode(args, tw, tdata, tstreams, dev, clocks=True, extras=False)
+            del bufs, tdata, tstreams
+            torch.cuda.empty_cache()
+            line["text256m"] = {"workload": _config(tw, args.format, 1, tw.size)["workload"], **tres}
+        line["batch_1gib"] = batch_result(args, GiB)
+        torch.cuda.empty_cache()
+        line["serving"] = serve_result(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def batch_result(args, cap):
     """Batched workload: many independent files of uneven sizes (log-uniform
-    4 KiB..16 MiB, seeded text/CSV and MRR/DE coins) decoded in ONE
-    persistent launch replayed from a CUDA graph, against one gmp_decompress
-    launch per file on the same stream.  Block size and sub-blocks per block
-    come from the format autotuner on a sample of the mix."""
+    4 KiB..16 MiB, seeded text/CSV and MRR/DE coins; the seeded prefix of the
+    4096-file list up to `cap` bytes, or all files for cap None) decoded in
+    ONE persistent launch replayed from a CUDA graph, against one
+    gmp_decompress launch per file on the same stream.  Block size and
+    sub-blocks per block come from the format autotuner on a sample of the
+    mix.  Returns the figures as a dict."""
     import torch
     import paper_1606_00519_gb300 as gmp
     from paper_1606_00519_gb300 import autotune
 
-    torch.cuda.set_device(0)
-    cap = None if args.batch_cap == 0 else args.batch_cap
     mix = datagen.file_mix(seed=4, n_files=args.batch_files, lo=4 * KiB, hi=16 * MiB, total_cap=cap)
     # a sample large enough to fill the GPU (the tuner times throughput, not
     # the latency of a small input): the first files of the mix, 128 MiB
@@ -525,17 +630,29 @@ def run_batch(args):
     torch.cuda.synchronize()
     per_file_ms = a.elapsed_time(b) / args.steps
     check()
-    line = {"metric": "batched decompressed GB/s", "value": round(total / (graph_ms / 1e3) / 1e9, 3), "unit": "GB/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(graph_ms, 4),
-            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"batch: {len(files)} files, log-uniform 4 KiB..16 MiB, text/CSV and MRR/DE mixed"
-                                   + (f", seeded prefix up to {cap} bytes" if cap else ""),
-                       "total_bytes": total, "compressed_bytes": comp_total, "ratio": round(total / comp_total, 4),
-                       "tuned": tuned, "tune_seconds": round(t_tune, 2),
-                       "launch_shape": {"warps_per_cta": shape["warps_per_cta"], "ctas_per_sm": shape["ctas_per_sm"]}},
+    graph.close()
+    ctx.close()
+    return {"metric": "batched decompressed GB/s", "value": round(total / (graph_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+            "steps": args.steps, "ms_per_step": round(graph_ms, 4),
+            "workload": f"batch: {len(files)} files, log-uniform 4 KiB..16 MiB, text/CSV and MRR/DE mixed"
+                        + (f", seeded prefix up to {cap} bytes" if cap else ""),
+            "total_bytes": total, "compressed_bytes": comp_total, "ratio": round(total / comp_total, 4),
+            "tuned": tuned, "tune_seconds": round(t_tune, 2),
+            "launch_shape": {"warps_per_cta": shape["warps_per_cta"], "ctas_per_sm": shape["ctas_per_sm"]},
             "one_launch_per_file": {"value": round(total / (per_file_ms / 1e3) / 1e9, 3), "unit": "GB/s",
                                     "ms_per_step": round(per_file_ms, 4)},
             "speedup_vs_one_launch_per_file": round(per_file_ms / graph_ms, 3)}
+
+
+def run_batch(args):
+    """The batched workload alone (bench.py --batch)."""
+    import torch
+    torch.cuda.set_device(0)
+    r = batch_result(args, None if args.batch_cap == 0 else args.batch_cap)
+    line = {"metric": r.pop("metric"), "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": 1,
+            "steps": r.pop("steps"), "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": r.pop("workload")}, **r}
     print(json.dumps(line), flush=True)
 
 
@@ -700,18 +817,17 @@ def run_compress(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
+def serve_result(args):
     """Serving: Poisson arrivals of requests (16 KiB..64 MiB, mixed content
     and modes) admitted under a device-memory budget by the continuous-batching
     server; p50/p99 latency (submit -> completion) and served GB/s at 25/50/90 %
     of the closed-loop peak, next to the same arrivals served one launch per
-    request."""
+    request.  Returns the figures as a dict."""
     import threading
 
     import torch
     import paper_1606_00519_gb300 as gmp
 
-    torch.cuda.set_device(0)
     # a seeded pool of distinct requests; the arrival sequence draws from it
     mix = datagen.request_mix(seed=5, n=args.serve_pool, lo=16 * KiB, hi=args.serve_max)
     pool = []
@@ -794,7 +910,16 @@ def run_serve(args):
         srv.close()
         result[name] = out
     result["value"] = result["batched"]["peak_gbs"]
-    print(json.dumps(result), flush=True)
+    return result
+
+
+def run_serve(args):
+    """The serving benchmark alone (bench.py --serve)."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(serve_result(args)), flush=True)
+
+
 
 
 def main():
@@ -803,7 +928,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmp", choices=["gmp", "reference"])
-    ap.add_argument("--workload", default="text256m", choices=sorted(datagen.WORKLOADS))
+    ap.add_argument("--workload", default="csv1g", choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--size", type=int, default=None, help="override bytes per stream")
     ap.add_argument("--format", default="bit", choices=["bit", "byte"],
                     help="stream format: Huffman blocks (bit) or byte-level blocks (byte)")
@@ -811,6 +936,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
     ap.add_argument("--ref-blocks", type=int, default=16, help="oracle blocks per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the main workload (no text256m, batch_1gib and serving sub-objects)")
+    ap.add_argument("--ref-pool", type=int, default=256 * MiB,
+                    help="reference arm: bytes of the workload compressed by the oracle per mode")
     ap.add_argument("--batch", action="store_true", help="batched many-file benchmark instead of the decode step")
     ap.add_argument("--batch-files", type=int, default=4096)
     ap.add_argument("--batch-cap", type=int, default=GiB, help="seeded prefix of the file list up to this many bytes "

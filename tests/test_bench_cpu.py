@@ -25,12 +25,13 @@ def _check(line):
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e = line["e2e"]
     assert e["value"] == line["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"].startswith("text256m")
+    assert line["config"]["workload"].startswith("csv1g")
+    assert line["config"]["bytes_per_stream"] == 1 << 30 and line["config"]["parallelism"].startswith("replicas")
 
 
 def test_reference_arm_line():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                        "--ref-blocks", "1"], cwd=ROOT, capture_output=True, text=True, timeout=500)
+                        "--ref-blocks", "1", "--ref-pool", str(8 << 20)], cwd=ROOT, capture_output=True, text=True, timeout=500)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _lines(r.stdout)
     assert len(lines) == 1
@@ -40,7 +41,8 @@ def test_reference_arm_line():
 def test_reference_arm_under_torchrun_prints_once():
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
                         "--master-addr", "127.0.0.1", "--master-port", "29571", "bench.py", "--impl", "reference",
-                        "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-blocks", "1"],
+                        "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-blocks", "1",
+                        "--ref-pool", str(8 << 20)],
                        cwd=ROOT, capture_output=True, text=True, timeout=500)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _lines(r.stdout)
