@@ -779,10 +779,13 @@ def run_sweep(args):
 
 
 def run_compress(args):
-    """Compression: the GPU parse (gmp_compress_gpu) against the host
-    compressor (gmp_compress, all host threads), host buffer to host buffer,
-    on the workload in both modes and formats; input GB/s and ratio, and the
-    decoded stream checked against the input on the GPU."""
+    """Compression: the GPU compressor (gmp_compress_gpu: match search, parse
+    and entropy coding on the device) against the host compressor
+    (gmp_compress, all host threads), host buffer to host buffer, on the
+    workload in both modes and formats; input GB/s and ratio, the GPU
+    compressor's device time per stage (input GB/s of the device work alone
+    and of its entropy coding), and the decoded stream checked against the
+    input on the GPU."""
     import torch
     import paper_1606_00519_gb300 as gmp
 
@@ -806,6 +809,12 @@ def run_compress(args):
                 if status != 0 or not np.array_equal(out.cpu().numpy(), data):
                     raise SystemExit(f"compress: {name} {fmt} {mode} stream does not decode to the input")
                 res[name] = {"gbs": round(data.size / sec / 1e9, 3), "ratio": round(data.size / st.size, 4)}
+                if name == "gpu":
+                    t = gmp.compress_gpu_times()
+                    dev_ms = t["match_ms"] + t["parse_ms"] + t["encode_ms"]
+                    res[name]["device_ms"] = {k: round(t[k], 3) for k in ("match_ms", "parse_ms", "encode_ms")}
+                    res[name]["device_gbs"] = round(data.size / dev_ms / 1e6, 3)
+                    res[name]["encode_gbs"] = round(data.size / t["encode_ms"] / 1e6, 3)
             row = {"format": fmt, "stream": mode, **res}
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)

@@ -172,20 +172,36 @@ size_t gmp_compress_bound(size_t n, const gmp_compress_opts* o);
 int gmp_compress(const void* host_in, size_t n, const gmp_compress_opts* o, void* host_out, size_t cap,
                  size_t* out_bytes);
 
-/* Compression with the LZ77 parse on the GPU `device` (Sec. 3.1: blocks are
-   compressed independently, so all of them at once; Sec. 4.2 for DE).  A
-   CTA per block finds, for 512 positions at a time, the longest match among
-   up to min(o->chain_depth, 64) earlier positions with the same 3-byte
-   prefix hash (input window, chain heads and links in shared memory); a
-   warp per block then parses (lazy evaluation, the DE rule when o->de,
-   1023-byte literal runs for Byte blocks); the host entropy-codes the parse
-   into the same stream format as gmp_compress (o->n_threads threads).
-   Positions of one step do not see each other, so ratios differ slightly
-   from gmp_compress's.  Host buffers; uses about 8 bytes of device memory
-   per input byte, freed before it returns.  Synchronous.  GMP_ERR_CUDA on
-   a CUDA failure (gmp_last_cuda_error). */
+/* Compression on the GPU `device`, every step of it (Sec. 3.1: blocks are
+   compressed independently, so all of them at once; Sec. 4.2 for DE).
+   Match search: a CTA per block finds, for 512 positions at a time, the
+   longest match among up to min(o->chain_depth, 64) earlier positions with
+   the same 3-byte prefix hash (input window, chain heads and links in shared
+   memory).  Parse: a warp per block (lazy evaluation, the DE rule when
+   o->de, 1023-byte literal runs for Byte blocks).  Entropy coding: a CTA
+   per block counts both alphabets, builds code lengths limited to o->cwl
+   bits (two-queue Huffman, then the bit-length adjustment of ITU-T T.81
+   Annex K.3), canonical codes, the sub-block split (equal decoding work) and
+   sizes, then packs each sub-block's codes at its bit offset; Byte blocks
+   get their records and literals.  The host lays the blocks out from their
+   sizes and writes the file header and block offset table; the stream
+   format is gmp_compress's.  Positions of one step do not see each other
+   and the code lengths are built differently, so ratios differ slightly
+   from gmp_compress's.  Host buffers; uses about 10 bytes of device memory
+   per input byte, freed before it returns.  Synchronous.  GMP_ERR_CUDA on a
+   CUDA failure (gmp_last_cuda_error), GMP_ERR_CAPACITY if cap is too small
+   (gmp_compress_bound). */
 int gmp_compress_gpu(int device, const void* host_in, size_t n, const gmp_compress_opts* o, void* host_out,
                      size_t cap, size_t* out_bytes);
+
+/* Device times (CUDA events) of the calling thread's last successful
+   gmp_compress_gpu: match search, parse, and entropy coding (planning and
+   writing every block), in milliseconds; all zero before the first call. */
+typedef struct {
+  double match_ms, parse_ms, encode_ms;
+  uint64_t compressed_bytes;
+} gmp_gpu_compress_times;
+void gmp_compress_gpu_last_times(gmp_gpu_compress_times* t);
 
 /* One-block stream holding a given LZ77 parse (the entropy-coding half of
    the compressor, for callers with their own match finder, and for streams

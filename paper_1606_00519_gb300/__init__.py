@@ -91,8 +91,8 @@ def compress(data, block_size: int = 256 << 10, n_sub: int = 32, window: int = 3
 def compress_gpu(data, block_size: int = 256 << 10, n_sub: int = 32, window: int = 32768, cwl: int = 12,
                  max_match: int = 64, de: bool = False, n_threads: int = 0, lazy: bool = True,
                  byte_mode: bool = False, device: int | None = None, chain_depth: int = 64) -> np.ndarray:
-    """Compress host bytes with the LZ77 parse on the GPU (gmp_compress_gpu):
-    same stream format as compress()."""
+    """Compress host bytes on the GPU (gmp_compress_gpu: match search, parse
+    and entropy coding on the device): same stream format as compress()."""
     L = _native.lib()
     src = _np_bytes(data)
     if device is None:
@@ -105,6 +105,15 @@ def compress_gpu(data, block_size: int = 256 << 10, n_sub: int = 32, window: int
     _check(L.gmp_compress_gpu(device, _ptr(src) if src.size else None, src.size, ctypes.byref(o), _ptr(out), cap,
                               ctypes.byref(n)), "gmp_compress_gpu")
     return out[:n.value]
+
+
+def compress_gpu_times() -> dict:
+    """Device times (ms) of this thread's last compress_gpu call: match
+    search, parse and entropy coding."""
+    t = _native.GpuCompressTimes()
+    _native.lib().gmp_compress_gpu_last_times(ctypes.byref(t))
+    return {"match_ms": t.match_ms, "parse_ms": t.parse_ms, "encode_ms": t.encode_ms,
+            "compressed_bytes": int(t.compressed_bytes)}
 
 
 def encode_tokens(lit_len, match_len, dist, lits, block_size: int | None = None, n_sub: int = 32,

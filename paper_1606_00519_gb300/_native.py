@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(BUILD, "libgmp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gmp_decode.cu", "gmp_host.cpp", "gmp_compress.cpp", "gmp_server.cpp", "gmp_noalloc.cu",
-           "gmp_gpucompress.cu"]
+           "gmp_gpucompress.cu", "gmp_gpuencode.cu"]
 
 _lock = threading.Lock()
 _lib = None
@@ -120,6 +120,11 @@ class Completion(ctypes.Structure):
                 ("t_done", ctypes.c_double)]
 
 
+class GpuCompressTimes(ctypes.Structure):
+    _fields_ = [("match_ms", ctypes.c_double), ("parse_ms", ctypes.c_double), ("encode_ms", ctypes.c_double),
+                ("compressed_bytes", ctypes.c_uint64)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("best_ms", ctypes.c_double),
                 ("shapes_tried", ctypes.c_uint32)]
@@ -145,6 +150,8 @@ def _declare(L):
     L.gmp_compress.argtypes = [vp, sz, P(CompressOpts), vp, sz, P(sz)]
     L.gmp_encode_tokens.argtypes = [vp, vp, vp, sz, vp, sz, P(CompressOpts), vp, sz, P(sz)]
     L.gmp_compress_gpu.argtypes = [i32, vp, sz, P(CompressOpts), vp, sz, P(sz)]
+    L.gmp_compress_gpu_last_times.argtypes = [P(GpuCompressTimes)]
+    L.gmp_compress_gpu_last_times.restype = None
     L.gmp_context_opts_default.argtypes = [P(ContextOpts)]
     L.gmp_context_opts_default.restype = None
     L.gmp_context_create.argtypes = [P(vp), i32, P(ContextOpts)]

@@ -371,31 +371,14 @@ void encode_block_byte(const uint8_t* in, uint32_t n, const std::vector<Seq>& se
 int assemble(const gmp_compress_opts& o, size_t n, const std::vector<std::vector<uint8_t>>& blocks, void* host_out,
              size_t cap, size_t* out_bytes) {
   const size_t nb = blocks.size();
-  uint64_t pos = (gmp::kHeaderBytes + 8 * nb + 15) & ~uint64_t(15);
-  uint64_t total = pos;
-  for (auto& b : blocks) total += b.size();
-  total += 16;
+  std::vector<uint64_t> sizes(nb), offsets(nb);
+  for (size_t b = 0; b < nb; b++) sizes[b] = blocks[b].size();
+  uint64_t total = 0;
+  gmp::stream_layout(sizes.data(), nb, offsets.data(), &total);
   if (total > cap) return GMP_ERR_CAPACITY;
   uint8_t* out = static_cast<uint8_t*>(host_out);
-  memset(out, 0, pos);
-  memcpy(out, "GMP1", 4);
-  put_le(out + 4, GMP_VERSION, 2);
-  put_le(out + 6, (o.de ? 1u : 0u) | (o.byte_mode ? 0u : 2u), 2);
-  put_le(out + 8, o.block_size, 4);
-  put_le(out + 12, o.byte_mode ? 0u : o.n_sub, 2);
-  out[14] = (uint8_t)(o.byte_mode ? 0u : o.cwl);
-  put_le(out + 16, o.window, 4);
-  out[20] = 3;
-  out[21] = (uint8_t)o.max_match;
-  put_le(out + 24, n, 8);
-  put_le(out + 32, nb, 8);
-  put_le(out + 40, total, 8);
-  for (size_t b = 0; b < nb; b++) {
-    put_le(out + gmp::kHeaderBytes + 8 * b, pos, 8);
-    memcpy(out + pos, blocks[b].data(), blocks[b].size());
-    pos += blocks[b].size();
-  }
-  memset(out + pos, 0, 16);
+  gmp::write_stream_header(o, n, nb, offsets.data(), total, out);
+  for (size_t b = 0; b < nb; b++) memcpy(out + offsets[b], blocks[b].data(), blocks[b].size());
   *out_bytes = total;
   return GMP_OK;
 }
@@ -411,69 +394,38 @@ bool opts_ok(const gmp_compress_opts& o) {
 
 namespace gmp {
 
-// Entropy coding and assembly of parses made elsewhere (the GPU match
-// finder): block b's parse is count[b] tokens at tok + first[b], token =
-// {literal length, (distance << 8) | match length}; literals are taken from
-// `in` in order.  Every token is checked against the block (lengths,
-// distances, sizes), so a faulty parse gives GMP_ERR_INVALID_ARG, never a
-// bad stream.  Blocks are encoded on o.n_threads host threads.
-int encode_token_blocks(const uint8_t* in, size_t n, const gmp_compress_opts& o, const ParseToken* tok,
-                        const uint32_t* count, const uint64_t* first, void* host_out, size_t cap, size_t* out_bytes) {
-  if (!opts_ok(o)) return GMP_ERR_INVALID_ARG;
-  const size_t nb = (n + o.block_size - 1) / o.block_size;
-  std::vector<std::vector<uint8_t>> blocks;
-  try {
-    blocks.resize(nb);
-  } catch (...) {
-    return GMP_ERR_NOMEM;
+bool compress_opts_ok(const gmp_compress_opts& o) { return opts_ok(o); }
+
+uint64_t stream_layout(const uint64_t* block_bytes, size_t nb, uint64_t* offsets, uint64_t* total) {
+  const uint64_t first = (kHeaderBytes + 8 * (uint64_t)nb + 15) & ~uint64_t(15);
+  uint64_t pos = first;
+  for (size_t b = 0; b < nb; b++) {
+    offsets[b] = pos;
+    pos += block_bytes[b];
   }
-  unsigned nt = o.n_threads ? o.n_threads : std::max(1u, std::thread::hardware_concurrency());
-  nt = (unsigned)std::min<size_t>(nt, std::max<size_t>(nb, 1));
-  std::atomic<size_t> next{0};
-  std::atomic<int> failed{GMP_OK};
-  auto worker = [&]() {
-    try {
-      std::vector<Seq> seqs;
-      for (;;) {
-        size_t b = next.fetch_add(1);
-        if (b >= nb || failed.load() != GMP_OK) break;
-        const size_t s0 = b * (size_t)o.block_size;
-        const uint32_t len = (uint32_t)std::min<size_t>(o.block_size, n - s0);
-        const ParseToken* t = tok + first[b];
-        seqs.clear();
-        uint64_t pos = 0;
-        for (uint32_t k = 0; k < count[b]; k++) {
-          const uint32_t ll = t[k].lit_len, ml = t[k].match & 0xffu, d = t[k].match >> 8;
-          const bool bad_match = ml && (ml < 3 || ml > o.max_match || d == 0 || d > o.window || d > pos + ll);
-          const bool bad_end = !ml && !o.byte_mode && k + 1 != count[b];
-          if (bad_match || bad_end || (o.byte_mode && ll > kByteMaxLit) || pos + ll + ml > len) {
-            failed = GMP_ERR_INVALID_ARG;
-            break;
-          }
-          seqs.push_back(Seq{(uint32_t)pos, ll, ml, ml ? d : 0});
-          pos += ll + ml;
-        }
-        if (failed.load() != GMP_OK) break;
-        if (pos != len) {
-          failed = GMP_ERR_INVALID_ARG;
-          break;
-        }
-        if (o.byte_mode) encode_block_byte(in + s0, len, seqs, blocks[b]);
-        else encode_block(in + s0, len, seqs, o, blocks[b]);
-      }
-    } catch (...) {
-      failed = GMP_ERR_NOMEM;
-    }
-  };
-  std::vector<std::thread> th;
-  for (unsigned t = 1; t < nt; t++) th.emplace_back(worker);
-  worker();
-  for (auto& t : th) t.join();
-  if (failed.load() != GMP_OK) return failed.load();
-  return assemble(o, n, blocks, host_out, cap, out_bytes);
+  *total = pos + 16;
+  return first;
 }
 
-bool compress_opts_ok(const gmp_compress_opts& o) { return opts_ok(o); }
+void write_stream_header(const gmp_compress_opts& o, size_t n, size_t nb, const uint64_t* offsets, uint64_t total,
+                         uint8_t* out) {
+  const uint64_t first = (kHeaderBytes + 8 * (uint64_t)nb + 15) & ~uint64_t(15);
+  memset(out, 0, first);
+  memcpy(out, "GMP1", 4);
+  put_le(out + 4, GMP_VERSION, 2);
+  put_le(out + 6, (o.de ? 1u : 0u) | (o.byte_mode ? 0u : 2u), 2);
+  put_le(out + 8, o.block_size, 4);
+  put_le(out + 12, o.byte_mode ? 0u : o.n_sub, 2);
+  out[14] = (uint8_t)(o.byte_mode ? 0u : o.cwl);
+  put_le(out + 16, o.window, 4);
+  out[20] = 3;
+  out[21] = (uint8_t)o.max_match;
+  put_le(out + 24, n, 8);
+  put_le(out + 32, nb, 8);
+  put_le(out + 40, total, 8);
+  for (size_t b = 0; b < nb; b++) put_le(out + kHeaderBytes + 8 * b, offsets[b], 8);
+  memset(out + total - 16, 0, 16);
+}
 
 }  // namespace gmp
 

@@ -2,10 +2,11 @@
 //
 // Sec. 3.1: the input is cut into blocks that are compressed independently,
 // hence in parallel; Sec. 4.2 adds the dependency rule of DE streams.  Here
-// the match search and the parse of every block run on the GPU, and the
-// entropy coding (Huffman trees and sub-blocks, or Byte records) runs on the
-// host from the GPU's parse (gmp::encode_token_blocks), writing the same
-// stream format as gmp_compress.
+// every step runs on the GPU: the match search and the parse of every block
+// (this file), then the entropy coding (Huffman trees and sub-blocks, or Byte
+// records; gmp_gpuencode.cu), writing the same stream format as
+// gmp_compress.  The host only lays out the blocks from their sizes and
+// writes the 64-byte file header and the block offset table.
 //
 //  match_kernel: one CTA per block.  The CTA walks the block 512 positions
 //  at a time, one per thread, with the block's bytes streaming through a ring
@@ -24,8 +25,8 @@
 //  back-reference of the same 32-sequence group writes, as in gmp_compress;
 //  for Byte streams literal strings are cut into runs of at most 1023
 //  bytes, which count as sequences of their group.
-//  pack_kernel: the blocks' token lists, packed back to back for the copy to
-//  the host.
+//  Every token's position in its block is written beside it for the
+//  entropy coder.
 //
 // Positions of the same step do not see each other, and one hash bucket per
 // prefix is shared by several prefixes, so the parse can differ from
@@ -190,8 +191,8 @@ constexpr uint32_t kChunk = 2048;  // positions staged in shared memory per warp
 __global__ void __launch_bounds__(32 * kParseWarps) parse_kernel(const uint8_t* best_len, const uint16_t* best_dist,
                                                                  uint64_t n, uint32_t block_size, uint64_t n_blocks,
                                                                  uint32_t max_match, int de, int byte_mode, int lazy,
-                                                                 gmp::ParseToken* tok, uint64_t stride,
-                                                                 uint32_t* count) {
+                                                                 gmp::ParseToken* tok, uint32_t* tpos,
+                                                                 uint64_t stride, uint32_t* count) {
   __shared__ uint8_t chunk_len[kParseWarps][kChunk];
   __shared__ uint16_t chunk_dist[kParseWarps][kChunk];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -202,12 +203,16 @@ __global__ void __launch_bounds__(32 * kParseWarps) parse_kernel(const uint8_t* 
   const uint64_t base = b * (uint64_t)block_size;
   const uint32_t len = (uint32_t)min((uint64_t)block_size, n - base);
   gmp::ParseToken* t = tok + b * stride;
+  uint32_t* tp = tpos + b * stride;
   uint32_t nt = 0, p = 0, lit_start = 0;
   ParseState st;
   st.in_grp = 0;
   st.lo_min = ~0u;
   auto emit = [&](uint32_t ll, uint32_t ml, uint32_t d) {
-    if (nt < stride) t[nt] = gmp::ParseToken{ll, (d << 8) | ml};
+    if (nt < stride) {
+      t[nt] = gmp::ParseToken{ll, (d << 8) | ml};
+      tp[nt] = lit_start;
+    }
     nt++;
   };
   auto add_to_group = [&](uint32_t lo, uint32_t hi) {
@@ -276,17 +281,11 @@ __global__ void __launch_bounds__(32 * kParseWarps) parse_kernel(const uint8_t* 
   }
 }
 
-// Copies block b's count[b] tokens to packed + first[b]; one CTA per block.
-__global__ void pack_kernel(const gmp::ParseToken* tok, uint64_t stride, const uint32_t* count, const uint64_t* first,
-                            gmp::ParseToken* packed) {
-  const uint64_t b = blockIdx.x;
-  const gmp::ParseToken* src = tok + b * stride;
-  gmp::ParseToken* dst = packed + first[b];
-  for (uint32_t k = threadIdx.x; k < count[b]; k += blockDim.x) dst[k] = src[k];
-}
+// Device times of the calling thread's last gmp_compress_gpu.
+thread_local gmp_gpu_compress_times g_times = {0, 0, 0, 0};
 
 struct DeviceBuffers {
-  void* p[8] = {};
+  void* p[12] = {};
   ~DeviceBuffers() {
     for (void* q : p)
       if (q) cudaFree(q);
@@ -304,7 +303,15 @@ int gmp_compress_gpu(int device, const void* host_in, size_t n, const gmp_compre
   if (!gmp::compress_opts_ok(o)) return GMP_ERR_INVALID_ARG;
   const uint8_t* in = static_cast<const uint8_t*>(host_in);
   const uint64_t nb = (n + o.block_size - 1) / o.block_size;
-  if (nb == 0) return gmp::encode_token_blocks(in, 0, o, nullptr, nullptr, nullptr, host_out, cap, out_bytes);
+  g_times = gmp_gpu_compress_times{0, 0, 0, 0};
+  if (nb == 0) {
+    uint64_t total = 0;
+    gmp::stream_layout(nullptr, 0, nullptr, &total);
+    if (total > cap) return GMP_ERR_CAPACITY;
+    gmp::write_stream_header(o, 0, 0, nullptr, total, static_cast<uint8_t*>(host_out));
+    *out_bytes = total;
+    return GMP_OK;
+  }
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
   cudaError_t e = cudaSetDevice(device);
@@ -314,35 +321,48 @@ int gmp_compress_gpu(int device, const void* host_in, size_t n, const gmp_compre
     // tokens per block: at most one per 3 bytes plus the literal-only runs
     const uint64_t stride = o.block_size / 3 + o.block_size / kByteMaxLit + 4;
     DeviceBuffers D;
-    uint8_t* d_in = nullptr;
-    uint8_t* d_len = nullptr;
-    uint16_t* d_dist = nullptr;
-    gmp::ParseToken* d_tok = nullptr;
-    uint32_t* d_count = nullptr;
-    unsigned long long* d_counter = nullptr;
+    cudaEvent_t ev[5] = {};
     auto check = [&](cudaError_t err, const char* what) {
       if (err != cudaSuccess && rc == GMP_OK) rc = gmp::cuda_error(err, what);
       return rc == GMP_OK;
     };
+    for (auto& x : ev) check(cudaEventCreate(&x), "cudaEventCreate");
     int sms = 0;
     check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "cudaDeviceGetAttribute");
+    uint8_t* d_in = nullptr;
+    uint8_t* d_len = nullptr;
+    uint16_t* d_dist = nullptr;
+    gmp::ParseToken* d_tok = nullptr;
+    uint32_t* d_tpos = nullptr;
+    uint32_t* d_count = nullptr;
+    unsigned long long* d_counter = nullptr;
+    gmp::EncBlockPlan* d_plan = nullptr;
+    uint64_t* d_bytes = nullptr;
     if (check(cudaMalloc(&D.p[0], n), "cudaMalloc") && check(cudaMalloc(&D.p[1], n), "cudaMalloc") &&
         check(cudaMalloc(&D.p[2], 2 * n), "cudaMalloc") &&
         check(cudaMalloc(&D.p[3], nb * stride * sizeof(gmp::ParseToken)), "cudaMalloc") &&
-        check(cudaMalloc(&D.p[4], nb * sizeof(uint32_t)), "cudaMalloc") &&
-        check(cudaMalloc(&D.p[5], sizeof(unsigned long long)), "cudaMalloc")) {
+        check(cudaMalloc(&D.p[4], nb * stride * sizeof(uint32_t)), "cudaMalloc") &&
+        check(cudaMalloc(&D.p[5], nb * sizeof(uint32_t)), "cudaMalloc") &&
+        check(cudaMalloc(&D.p[6], 2 * sizeof(unsigned long long)), "cudaMalloc") &&
+        check(cudaMalloc(&D.p[7], nb * sizeof(gmp::EncBlockPlan)), "cudaMalloc") &&
+        check(cudaMalloc(&D.p[8], nb * sizeof(uint64_t)), "cudaMalloc")) {
       d_in = static_cast<uint8_t*>(D.p[0]);
       d_len = static_cast<uint8_t*>(D.p[1]);
       d_dist = static_cast<uint16_t*>(D.p[2]);
       d_tok = static_cast<gmp::ParseToken*>(D.p[3]);
-      d_count = static_cast<uint32_t*>(D.p[4]);
-      d_counter = static_cast<unsigned long long*>(D.p[5]);
+      d_tpos = static_cast<uint32_t*>(D.p[4]);
+      d_count = static_cast<uint32_t*>(D.p[5]);
+      d_counter = static_cast<unsigned long long*>(D.p[6]);
+      d_plan = static_cast<gmp::EncBlockPlan*>(D.p[7]);
+      d_bytes = static_cast<uint64_t*>(D.p[8]);
     }
+    int* d_error = reinterpret_cast<int*>(d_counter + 1);
     if (rc == GMP_OK) {
       check(cudaMemcpy(d_in, in, n, cudaMemcpyHostToDevice), "cudaMemcpy");
-      check(cudaMemset(d_counter, 0, sizeof(unsigned long long)), "cudaMemset");
+      check(cudaMemset(d_counter, 0, 2 * sizeof(unsigned long long)), "cudaMemset");
     }
     if (rc == GMP_OK) {
+      check(cudaEventRecord(ev[0]), "cudaEventRecord");
       const int smem = (int)sizeof(MatchSmem);
       int occ = 0;
       check(cudaFuncSetAttribute(match_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
@@ -358,48 +378,62 @@ int gmp_compress_gpu(int device, const void* host_in, size_t n, const gmp_compre
       }
     }
     if (rc == GMP_OK) {
+      check(cudaEventRecord(ev[1]), "cudaEventRecord");
       parse_kernel<<<(unsigned)((nb + kParseWarps - 1) / kParseWarps), 32 * kParseWarps>>>(
           d_len, d_dist, n, o.block_size, nb, o.max_match, o.de ? 1 : 0, o.byte_mode ? 1 : 0, o.lazy ? 1 : 0, d_tok,
-          stride, d_count);
+          d_tpos, stride, d_count);
       check(cudaGetLastError(), "parse_kernel");
     }
-    std::vector<uint32_t> count(nb);
-    std::vector<uint64_t> first(nb + 1, 0);
-    if (rc == GMP_OK) check(cudaMemcpy(count.data(), d_count, nb * sizeof(uint32_t), cudaMemcpyDeviceToHost),
+    // entropy coding on the GPU: plan every block (sizes), lay the blocks out
+    // on the host, write them
+    gmp::EncLaunch L{d_in, n, o.block_size, o.byte_mode ? 0u : o.n_sub, o.cwl, o.window, o.max_match,
+                     o.byte_mode ? 1 : 0, nb, d_tok, d_tpos, stride, d_count, d_plan, d_bytes, d_error,
+                     (unsigned)std::min<uint64_t>(nb, (uint64_t)std::max(sms, 1) * 8), nullptr};
+    if (rc == GMP_OK) {
+      check(cudaEventRecord(ev[2]), "cudaEventRecord");
+      check(gmp::launch_encode_plan(L), "plan_kernel");
+    }
+    std::vector<uint64_t> sizes(nb), offsets(nb);
+    int h_error = 0;
+    if (rc == GMP_OK) check(cudaMemcpy(sizes.data(), d_bytes, nb * sizeof(uint64_t), cudaMemcpyDeviceToHost),
                             "cudaMemcpy");
+    if (rc == GMP_OK) check(cudaMemcpy(&h_error, d_error, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (rc == GMP_OK && h_error) rc = GMP_ERR_INVALID_ARG;  // a parse that fails its checks (not expected)
+    uint64_t total = 0, first = 0;
     if (rc == GMP_OK) {
-      for (uint64_t b = 0; b < nb; b++) {
-        if (count[b] > stride) rc = GMP_ERR_INVALID_ARG;  // cannot happen: a parse has at most `stride` tokens
-        first[b + 1] = first[b] + count[b];
-      }
+      first = gmp::stream_layout(sizes.data(), nb, offsets.data(), &total);
+      if (total > cap) rc = GMP_ERR_CAPACITY;
     }
-    std::vector<gmp::ParseToken> host_tok;
-    if (rc == GMP_OK) {
-      try {
-        host_tok.resize(std::max<uint64_t>(first[nb], 1));
-      } catch (...) {
-        rc = GMP_ERR_NOMEM;
-      }
-    }
-    if (rc == GMP_OK && check(cudaMalloc(&D.p[6], std::max<uint64_t>(first[nb], 1) * sizeof(gmp::ParseToken)),
-                              "cudaMalloc") &&
-        check(cudaMalloc(&D.p[7], nb * sizeof(uint64_t)), "cudaMalloc")) {
-      uint64_t* d_first = static_cast<uint64_t*>(D.p[7]);
-      gmp::ParseToken* d_packed = static_cast<gmp::ParseToken*>(D.p[6]);
-      check(cudaMemcpy(d_first, first.data(), nb * sizeof(uint64_t), cudaMemcpyHostToDevice), "cudaMemcpy");
+    const uint64_t body = total - first - 16;  // the blocks, back to back
+    if (rc == GMP_OK && check(cudaMalloc(&D.p[9], std::max<uint64_t>(body, 16)), "cudaMalloc") &&
+        check(cudaMalloc(&D.p[10], nb * sizeof(uint64_t)), "cudaMalloc")) {
+      uint64_t* d_off = static_cast<uint64_t*>(D.p[10]);
+      for (uint64_t b = 0; b < nb; b++) offsets[b] -= first;
+      check(cudaMemcpy(d_off, offsets.data(), nb * sizeof(uint64_t), cudaMemcpyHostToDevice), "cudaMemcpy");
+      if (rc == GMP_OK) check(gmp::launch_encode_write(L, d_off, static_cast<uint8_t*>(D.p[9])), "write_kernel");
+      if (rc == GMP_OK) check(cudaEventRecord(ev[3]), "cudaEventRecord");
+      uint8_t* out = static_cast<uint8_t*>(host_out);
+      if (rc == GMP_OK) check(cudaMemcpy(out + first, D.p[9], body, cudaMemcpyDeviceToHost), "cudaMemcpy");
       if (rc == GMP_OK) {
-        pack_kernel<<<(unsigned)nb, 256>>>(d_tok, stride, d_count, d_first, d_packed);
-        check(cudaGetLastError(), "pack_kernel");
+        for (uint64_t b = 0; b < nb; b++) offsets[b] += first;
+        gmp::write_stream_header(o, n, nb, offsets.data(), total, out);
+        *out_bytes = total;
+        float t = 0;
+        if (cudaEventElapsedTime(&t, ev[0], ev[1]) == cudaSuccess) g_times.match_ms = t;
+        if (cudaEventElapsedTime(&t, ev[1], ev[2]) == cudaSuccess) g_times.parse_ms = t;
+        if (cudaEventElapsedTime(&t, ev[2], ev[3]) == cudaSuccess) g_times.encode_ms = t;
+        g_times.compressed_bytes = total;
       }
-      if (rc == GMP_OK)
-        check(cudaMemcpy(host_tok.data(), d_packed, first[nb] * sizeof(gmp::ParseToken), cudaMemcpyDeviceToHost),
-              "cudaMemcpy");
     }
-    if (rc == GMP_OK)
-      rc = gmp::encode_token_blocks(in, n, o, host_tok.data(), count.data(), first.data(), host_out, cap, out_bytes);
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
   }
   if (prev >= 0) cudaSetDevice(prev);
   return rc;
+}
+
+void gmp_compress_gpu_last_times(gmp_gpu_compress_times* t) {
+  if (t) *t = g_times;
 }
 
 }  // extern "C"

@@ -51,8 +51,43 @@ constexpr uint32_t kPipeParts = 8;
 struct ParseToken {
   uint32_t lit_len, match;
 };
-int encode_token_blocks(const uint8_t* in, size_t n, const gmp_compress_opts& o, const ParseToken* tok,
-                        const uint32_t* count, const uint64_t* first, void* host_out, size_t cap, size_t* out_bytes);
+// GPU entropy coding of GPU parses (gmp_gpuencode.cu): per block, a plan
+// (token checks, code lengths, sub-block split and sizes), then the block's
+// bytes at an offset computed from the planned sizes.
+struct EncBlockPlan {
+  uint64_t bytes, bits;  // encoded size (a multiple of 16), bitstream bits
+  uint32_t n_seq, out_bytes, n_lit, err;
+  uint32_t sub_first[kMaxSub + 1];  // first token of each sub-block; [K] = n_seq
+  uint32_t sub_out[kMaxSub];        // output bytes of each sub-block
+  uint64_t sub_bits[kMaxSub];       // bits of each sub-block
+  uint8_t lens[kLitLenSyms + kOffsetSyms];
+};
+struct EncLaunch {
+  const uint8_t* in;  // device input
+  uint64_t n;
+  uint32_t block_size, n_sub, cwl, window, max_match;
+  int byte_mode;
+  uint64_t n_blocks;
+  const ParseToken* tok;  // block b's tokens at tok + b * stride
+  const uint32_t* tpos;   // block-relative position of each token's literals
+  uint64_t stride;
+  const uint32_t* count;  // tokens per block
+  EncBlockPlan* plan;
+  uint64_t* block_bytes;  // encoded size per block
+  int* error;             // set to 1 if a token fails its checks
+  unsigned grid;
+  cudaStream_t stream;
+};
+cudaError_t launch_encode_plan(const EncLaunch& L);
+cudaError_t launch_encode_write(const EncLaunch& L, const uint64_t* offsets, uint8_t* out);
+// Stream layout (gmp_compress.cpp): block offsets (absolute, 16-byte
+// aligned) after the header and offset table, and the total size with the
+// tail padding; returns the first block's offset.
+uint64_t stream_layout(const uint64_t* block_bytes, size_t nb, uint64_t* offsets, uint64_t* total);
+// The file header and block offset table at out[0 ..), and the 16 zero bytes
+// of tail padding at out[total - 16 ..).
+void write_stream_header(const gmp_compress_opts& o, size_t n, size_t nb, const uint64_t* offsets, uint64_t total,
+                         uint8_t* out);
 bool compress_opts_ok(const gmp_compress_opts& o);
 // records a CUDA failure for gmp_last_cuda_error; returns GMP_ERR_CUDA
 int cuda_error(cudaError_t e, const char* what);

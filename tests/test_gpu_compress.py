@@ -1,9 +1,12 @@
-"""GPU tests of the compressor with the LZ77 parse on the GPU
-(gmp_compress_gpu; Sec. 3.1 block-parallel compression, Sec. 4.2 DE): every
-stream it writes passes the oracle's validators (Kraft equality, window and
-block bounds, the DE property for DE streams), decodes to the input in the
-oracle and on the GPU, in both formats and modes, at edge sizes and on
-degenerate data; the output is deterministic."""
+"""GPU tests of the compressor that runs on the GPU end to end
+(gmp_compress_gpu; Sec. 3.1 block-parallel compression and the two Huffman
+trees per block, Sec. 4.2 DE): every stream it writes passes the oracle's
+validators (Kraft equality and code lengths within the limit for both trees
+of every block, window and block bounds, sub-block sizes, the DE property
+for DE streams), decodes to the input in the oracle and on the GPU, in both
+formats and modes, at edge sizes and on degenerate data (single-symbol
+alphabets, incompressible blocks that are one literal run); the output is
+deterministic and the entropy coding ran on the device."""
 import numpy as np
 import pytest
 
@@ -59,6 +62,25 @@ def test_workloads(gmp, ctx, name, mode, byte_mode):
     assert s.size < 1.35 * ref.size
     # deterministic
     assert np.array_equal(gmp.compress_gpu(data, w.block_size, w.n_sub, w.window, de=de, byte_mode=byte_mode), s)
+    t = gmp.compress_gpu_times()
+    assert t["match_ms"] > 0 and t["parse_ms"] > 0 and t["encode_ms"] > 0 and t["compressed_bytes"] == s.size
+
+
+@pytest.mark.parametrize("cwl", [9, 10, 12])
+def test_code_length_limit(gmp, ctx, cwl):
+    """Skewed symbol frequencies whose unconstrained Huffman code is deeper
+    than the limit: the lengths are cut to cwl bits and stay complete."""
+    rng = np.random.default_rng(cwl)
+    # literal frequencies falling geometrically (depth ~ 20 unconstrained)
+    p = 0.6 ** np.arange(64)
+    data = rng.choice(64, size=400_000, p=p / p.sum()).astype(np.uint8)
+    for de in (False, True):
+        s = gmp.compress_gpu(data, 64 * KiB, 16, 8 * KiB, cwl=cwl, de=de)
+        rep = oracle.validate(s)
+        assert rep["rc"] == 0 and rep["kraft_ok"] and rep["lengths_ok"], rep
+        assert np.array_equal(oracle.decompress(s), data)
+        got, st = ctx.decompress(gmp.DeviceStream(s))
+        assert st == 0 and np.array_equal(got.cpu().numpy(), data)
 
 
 @pytest.mark.parametrize("size", [0, 1, 2, 3, 31, 32, 33, 1000, 65535, 65536, 65537, 200_003])
