@@ -110,3 +110,38 @@ def test_request_larger_than_budget_is_refused(gmp, requests):
     with pytest.raises(gmp.GmpError):
         srv.submit(s)
     srv.close()
+
+
+def test_serving_shape_of_the_load_configuration(gmp):
+    """The serving configuration's request shape: sizes log-uniform from
+    16 KiB to 64 MiB, mixed content and modes, arriving while others run,
+    under a budget that holds only some of them (2 GiB here instead of 32).
+    Several lanes must be busy at the same time (their batches' launch-to-
+    completion intervals overlap), and every output must equal the input and
+    the same request decoded alone (tolerance: 0 bytes)."""
+    mix = datagen.request_mix(seed=21, n=40, lo=16 * KiB, hi=64 * MiB)
+    reqs = []
+    for size, kind, mode, sd in mix:
+        data = datagen.make_data(kind, size, sd)
+        reqs.append((data, gmp.compress(data, 256 * KiB, 32, 32 * KiB, de=(mode == "de"))))
+    assert max(d.size for d, _ in reqs) > 32 * MiB
+    srv = gmp.Server(budget_bytes=2 << 30, n_lanes=4, max_batch=8)
+    mixed = _run(gmp, srv, reqs, spacing_s=0.0005)
+    assert len(mixed) == len(reqs)
+    spans = []
+    for i, (data, _) in enumerate(reqs):
+        c, got = mixed[i]
+        assert c["status"] == 0 and np.array_equal(got, data)
+        spans.append((c["t_start"], c["t_done"]))
+    # distinct launches (requests of one batch share theirs) whose launch-to-
+    # completion intervals overlap: batches of different lanes in flight at
+    # the same time
+    launches = sorted(set(spans))
+    overlaps = sum(1 for a, b in zip(launches, launches[1:]) if b[0] < a[1])
+    assert len(launches) >= 2 and overlaps >= 1
+    # the largest requests again, alone
+    for i in sorted(range(len(reqs)), key=lambda k: -reqs[k][0].size)[:4]:
+        alone = _run(gmp, srv, [reqs[i]])
+        assert np.array_equal(alone[0][1], mixed[i][1])
+    assert srv.bytes_in_use() == 0
+    srv.close()
