@@ -826,6 +826,25 @@ def run_compress(args):
     print(json.dumps(line), flush=True)
 
 
+def _concurrency(spans):
+    """Batched launches in flight at once, from each distinct launch's
+    (launch time, completion time) on the host clock (requests of one batch
+    share their launch): the largest count over time and the time-weighted
+    mean while any launch is in flight."""
+    ev = sorted([(a, 1) for a, b in spans] + [(b, -1) for a, b in spans])
+    cur = peak = 0
+    busy = area = 0.0
+    last = None
+    for t, d in ev:
+        if last is not None and cur > 0:
+            busy += t - last
+            area += cur * (t - last)
+        cur += d
+        peak = max(peak, cur)
+        last = t
+    return {"launches": len(spans), "max": peak, "mean": round(area / busy, 3) if busy > 0 else 0.0}
+
+
 def serve_result(args):
     """Serving: Poisson arrivals of requests (16 KiB..64 MiB, mixed content
     and modes) admitted under a device-memory budget by the continuous-batching
@@ -853,6 +872,7 @@ def serve_result(args):
         total bytes, wall seconds; checks every output's size and status, and
         the bytes of a sample."""
         lat, done, nbytes = [], 0, 0
+        spans = set()
         ids = {}
         errors = []
         lock = threading.Lock()
@@ -871,6 +891,7 @@ def serve_result(args):
                         if not np.array_equal(buf, pool[picks[i]][2]):
                             errors.append((i, "bytes"))
                     lat.append(c["t_done"] - c["t_submit"])
+                    spans.add((c["t_start"], c["t_done"]))
                     nbytes += c["out_bytes"]
                     server.release(c["id"])
                     done += 1
@@ -888,6 +909,7 @@ def serve_result(args):
         wall = time.perf_counter() - t0
         if errors:
             raise SystemExit(f"serve: {len(errors)} bad results, e.g. {errors[:3]}")
+        run.last_concurrency = _concurrency(spans)
         return np.array(lat), nbytes, wall
 
     n = args.serve_requests
@@ -907,7 +929,7 @@ def serve_result(args):
         # that the first and last batches do not dominate)
         lat, nb, wall = run(srv, np.zeros(n), picks)
         peak = nb / wall / 1e9
-        out = {"peak_gbs": round(peak, 3)}
+        out = {"peak_gbs": round(peak, 3), "peak_launches_in_flight": run.last_concurrency}
         for load in (0.25, 0.5, 0.9):
             rate = load * peak * 1e9 / mean_size
             arr = datagen.poisson_arrivals(seed=int(load * 100), n=n, rate_per_s=rate)
@@ -915,7 +937,8 @@ def serve_result(args):
             out[f"load_{int(load * 100)}"] = {"offered_req_per_s": round(rate, 1),
                                               "served_gbs": round(nb / wall / 1e9, 3),
                                               "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
-                                              "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
+                                              "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                                              "launches_in_flight": run.last_concurrency}
         srv.close()
         result[name] = out
     result["value"] = result["batched"]["peak_gbs"]

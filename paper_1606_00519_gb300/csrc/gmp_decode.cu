@@ -682,6 +682,10 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
         q_end = q + S.u.a.sb_seqn[j];
         act = q < q_end;
       }
+      // The bit buffer is refilled to more than 32 bits before each
+      // literal/length code, so that a code (<= 12 bits) and, after it, an
+      // offset code with its extra bits (<= 12 + 13) rarely need a second
+      // refill: fewer divergent branches per step.
       while (__any_sync(FULL, act)) {
   #ifdef GMP_PHASE_TIMERS
         tdet[5]++;
@@ -689,7 +693,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
         // two symbols per lane per warp step (the second only if the lane is
         // still active), halving the votes and reconvergence points
         if (act) {
-          if (nb < 32) {
+          if (nb <= 32) {
             buf |= (uint64_t)next_word() << nb;
             nb += 32;
           }
@@ -709,7 +713,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
             uint32_t ml = 0, dist = 0;
             if (sym > 256) {
               ml = sym - 254u;
-              if (nb < 32) {
+              if (nb < 25) {
                 buf |= (uint64_t)next_word() << nb;
                 nb += 32;
               }
@@ -743,7 +747,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
           act = !err && q < q_end;
         }
         if (act) {  // second symbol of the step
-          if (nb < 32) {
+          if (nb <= 32) {
             buf |= (uint64_t)next_word() << nb;
             nb += 32;
           }
@@ -763,7 +767,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
             uint32_t ml = 0, dist = 0;
             if (sym > 256) {
               ml = sym - 254u;
-              if (nb < 32) {
+              if (nb < 25) {
                 buf |= (uint64_t)next_word() << nb;
                 nb += 32;
               }

@@ -48,3 +48,14 @@ def test_reference_arm_under_torchrun_prints_once():
     lines = _lines(r.stdout)
     assert len(lines) == 1
     _check(lines[0])
+
+
+def test_launches_in_flight_from_spans():
+    """The serving line's overlap figure: launches in flight at once, from
+    each distinct launch's (start, completion) host times."""
+    import bench
+    c = bench._concurrency({(0.0, 2.0), (1.0, 3.0), (2.5, 4.0), (5.0, 6.0)})
+    assert c == {"launches": 4, "max": 2, "mean": 1.3}
+    assert bench._concurrency(set()) == {"launches": 0, "max": 0, "mean": 0.0}
+    # one launch at a time, back to back
+    assert bench._concurrency({(0.0, 1.0), (1.0, 2.0)})["max"] == 1
