@@ -369,14 +369,10 @@ struct SrcView {
   }
 };
 
-__device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v, uint32_t rpos, uint32_t wpos,
-                                                 uint32_t ml) {
-  const bool in_ring = rpos >= v.ring_lo;                                      // whole source in the ring
-  const bool in_far = !in_ring && rpos >= v.far_lo && rpos + ml <= v.far_hi;   // whole source staged
-  if (!(in_ring || in_far)) {
-    for (uint32_t i = 0; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
-    return;
-  }
+// The copy with every access wrapped by the ring mask (a source wholly in
+// the ring, in_ring, or wholly in the lane's far staging).
+__device__ __forceinline__ void copy_match_masked(uint8_t* ring, const SrcView& v, uint32_t rpos, uint32_t wpos,
+                                                  uint32_t ml, bool in_ring) {
   // one linear view of the source: byte x at base[(x - off) & mask], word a
   // (bytes 4a .. 4a + 3 of the view) at base32[a & wmask]; the staging is
   // 16-byte aligned, so a source's offset within its word is x & 3 either way
@@ -405,7 +401,7 @@ __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v
   uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
   const uint32_t nw = (ml - h) >> 2;  // whole aligned destination words
   const uint32_t x0 = rpos + h - off, d0 = (wpos + h) >> 2, sh = ((rpos + h) & 3u) * 8u;
-  if (dist >= 16 || in_far) {
+  if (dist >= 16 || !in_ring) {
     // four words per step: a step's 16 source bytes lie before its
     // destination (or in the staging), so its five loads issue together and
     // a copy of up to 16 bytes takes one shared-memory latency
@@ -435,6 +431,77 @@ __device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v
     if (t > 1) ring[(wpos + i + 1u) & RING_MASK] = b1;
     if (t > 2) ring[(wpos + i + 2u) & RING_MASK] = b2;
   }
+}
+
+__device__ __forceinline__ void copy_match_words(uint8_t* ring, const SrcView& v, uint32_t rpos, uint32_t wpos,
+                                                 uint32_t ml) {
+  const bool in_ring = rpos >= v.ring_lo;                                      // whole source in the ring
+  const bool in_far = !in_ring && rpos >= v.far_lo && rpos + ml <= v.far_hi;   // whole source staged
+  if (!(in_ring || in_far)) {
+    for (uint32_t i = 0; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+    return;
+  }
+  copy_match_masked(ring, v, rpos, wpos, ml, in_ring);
+}
+
+// Out of line, for copy_match_linear's rare cases (a source or destination
+// that crosses the ring's end, or a ring source closer than 16 bytes).
+__device__ __noinline__ void copy_match_general(uint8_t* ring, const SrcView v, uint32_t rpos, uint32_t wpos,
+                                                uint32_t ml, bool in_ring) {
+  copy_match_masked(ring, v, rpos, wpos, ml, in_ring);
+}
+
+// copy_match_words with the common case in linear addressing (used by the
+// 128-register kernel instance, whose registers hold it without spilling).
+__device__ __forceinline__ void copy_match_linear(uint8_t* ring, const SrcView& v, uint32_t rpos, uint32_t wpos,
+                                                 uint32_t ml) {
+  const bool in_ring = rpos >= v.ring_lo;                                      // whole source in the ring
+  const bool in_far = !in_ring && rpos >= v.far_lo && rpos + ml <= v.far_hi;   // whole source staged
+  if (!(in_ring || in_far)) {
+    for (uint32_t i = 0; i < ml; i++) ring[(wpos + i) & RING_MASK] = v.byte(rpos + i);
+    return;
+  }
+  // Linear case: the destination and (for a ring source) the source plus
+  // the 16 bytes its word loads may read past it do not cross the ring's end,
+  // and the distance is at least 16 (a far source is more than NEAR bytes
+  // back), so that no source word holds bytes this copy writes in the same
+  // step.  Every access is then one base register plus an immediate offset.
+  {
+    const uint32_t rs = rpos & RING_MASK, ws = wpos & RING_MASK;
+    if ((in_far || (wpos - rpos >= 16u && rs + ml + 16u <= (uint32_t)RING)) && ws + ml <= (uint32_t)RING) {
+      const uint8_t* src = in_ring ? ring + rs : v.far + (rpos - v.far_lo);
+      uint8_t* dst = ring + ws;
+      // head: up to the destination's next 4-byte boundary
+      const uint32_t h = min(ml, (4u - (wpos & 3u)) & 3u);
+      {
+        const uint8_t b0 = src[0], b1 = src[1], b2 = src[2];
+        if (h > 0) dst[0] = b0;
+        if (h > 1) dst[1] = b1;
+        if (h > 2) dst[2] = b2;
+      }
+      // whole destination words, four per step, from unaligned source words
+      const uint32_t nw = (ml - h) >> 2;
+      const uintptr_t sp = reinterpret_cast<uintptr_t>(src + h);
+      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(sp & ~static_cast<uintptr_t>(3));
+      const uint32_t sh = static_cast<uint32_t>(sp & 3u) * 8u;
+      uint32_t* d32 = reinterpret_cast<uint32_t*>(dst + h);
+      for (uint32_t k = 0; k < nw; k += 4) {
+        const uint32_t w0 = s32[k], w1 = s32[k + 1], w2 = s32[k + 2], w3 = s32[k + 3], w4 = s32[k + 4];
+        d32[k] = __funnelshift_r(w0, w1, sh);
+        if (k + 1 < nw) d32[k + 1] = __funnelshift_r(w1, w2, sh);
+        if (k + 2 < nw) d32[k + 2] = __funnelshift_r(w2, w3, sh);
+        if (k + 3 < nw) d32[k + 3] = __funnelshift_r(w3, w4, sh);
+      }
+      // tail: fewer than 4 bytes
+      const uint32_t i = h + 4u * nw, t = ml - i;
+      const uint8_t b0 = src[i], b1 = src[i + 1], b2 = src[i + 2];
+      if (t > 0) dst[i] = b0;
+      if (t > 1) dst[i + 1] = b1;
+      if (t > 2) dst[i + 2] = b2;
+      return;
+    }
+  }
+  copy_match_general(ring, v, rpos, wpos, ml, in_ring);
 }
 
 // Out-of-line resolutions, kept out of the decode loop's code: Sequential
@@ -827,10 +894,14 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
   unsigned long long* rstat = STATS ? S.rstat : nullptr;
   const uint32_t n_groups_total = (n_seq + 31) / 32;
 
+  // A group's per-lane values, packed to keep the two live copies (the group
+  // being resolved and the one being staged) small: w = (distance << 8) |
+  // match length as in the records; far = staged window start (16-byte
+  // aligned) | its 16-byte chunk count; lit = literal staging start (16-byte
+  // aligned) | staged flag (bit 0) | (Byte blocks) a failed check's status
+  // << 1.  Write position = dst + ll, source = write position - distance.
   struct Prep {
-    uint32_t ll, ml, dst, lsrc, wpos, rpos, gtot, glits, far_lo, far_hi, lit_lo;
-    int err;  // Byte blocks: the group's records failed a check (a gmp_status)
-    bool valid, lit_staged;
+    uint32_t ll, w, dst, lsrc, gtot, glits, far, lit;
   };
   // sequence t: Huffman blocks {output position, literal source, literal
   // length, (distance << 8) | match length} from phase A; Byte blocks
@@ -848,19 +919,20 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
   auto prep = [&](uint32_t h, uint4 r, uint32_t G0h, uint32_t litposh, bool allow, int stage) {
     Prep q;
     const uint32_t t = h * 32 + lane;
-    q.valid = t < n_seq;
+    const bool valid = t < n_seq;
     q.ll = r.z;
-    q.ml = r.w & 0xffu;
+    q.w = r.w;
+    const uint32_t ml = r.w & 0xffu;
     const uint32_t dist = r.w >> 8;
     // the group's literal run in the literal source, [lit_a, lit_b), and
     // whether the group's literals lie in it back to back
     uint32_t lit_a, lit_b;
     bool lit_run;
     if (!byte_fmt) {
-      q.gtot = __reduce_max_sync(FULL, q.valid ? r.x + q.ll + q.ml : G0h) - G0h;
+      q.gtot = __reduce_max_sync(FULL, valid ? r.x + q.ll + ml : G0h) - G0h;
       // lanes past the block's last sequence sit at the group's end, so that
       // write positions never fall with the lane
-      q.dst = q.valid ? r.x : G0h + q.gtot;
+      q.dst = valid ? r.x : G0h + q.gtot;
       q.lsrc = r.y;
       q.glits = __reduce_add_sync(FULL, q.ll);
       lit_a = __reduce_min_sync(FULL, q.ll ? q.lsrc : 0xffffffffu);
@@ -869,7 +941,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
     } else {
       // one reduction and one scan of (literal length << 16 | total length):
       // a record's lengths are below 2^11, a group's sums below 2^16
-      const uint32_t packed = (q.ll << 16) | (q.ll + q.ml);
+      const uint32_t packed = (q.ll << 16) | (q.ll + ml);
       const uint32_t sum = __reduce_add_sync(FULL, packed);
       const uint32_t inc = warp_incl_scan(packed) - packed;
       q.gtot = sum & 0xffffu;
@@ -880,34 +952,31 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
       lit_b = litposh + q.glits;
       lit_run = true;
     }
-    q.wpos = q.dst + q.ll;
-    q.rpos = q.wpos - dist;
-    q.far_lo = q.far_hi = 0;
-    q.lit_lo = 0;
-    q.lit_staged = false;
-    q.err = 0;
+    const uint32_t wpos = q.dst + q.ll, rpos = wpos - dist;
+    q.far = 0;
+    q.lit = 0;
+    int err = 0;
     if (byte_fmt) {
       // phase A checks Huffman records as it decodes them; Byte records are
       // checked here, before anything is staged or copied for the group
-      if (__any_sync(FULL, q.ml > max_match)) q.err = GMP_STATUS_CORRUPT_SYMBOL;
-      else if (__any_sync(FULL, q.ml > 0 && (dist > window || dist > q.wpos))) q.err = GMP_STATUS_BAD_OFFSET;
+      if (__any_sync(FULL, ml > max_match)) err = GMP_STATUS_CORRUPT_SYMBOL;
+      else if (__any_sync(FULL, ml > 0 && (dist > window || dist > wpos))) err = GMP_STATUS_BAD_OFFSET;
       else if ((uint64_t)G0h + q.gtot > out_bytes || (uint64_t)litposh + q.glits > n_lit)
-        q.err = GMP_STATUS_OUTPUT_OVERRUN;
-      if (q.err) allow = false;
+        err = GMP_STATUS_OUTPUT_OVERRUN;
+      if (err) allow = false;
     }
     if (allow && vec_ok && q.gtot <= GROUP_FAST_MAX) {
       // far part of the source: below the ring's reach, already in device memory
       const uint32_t rlo = max(ring_valid_lo, G0h > NEAR ? G0h - NEAR : 0u);
-      if (q.ml > 0 && q.rpos < rlo) {
-        const uint32_t fe = min(q.rpos + q.ml, rlo);
-        const uint32_t a0 = q.rpos & ~15u;
+      if (ml > 0 && rpos < rlo) {
+        const uint32_t fe = min(rpos + ml, rlo);
+        const uint32_t a0 = rpos & ~15u;
         const uint32_t a1 = min((fe + 15u) & ~15u, flushed & ~15u);
         uint8_t* dstage = SB.far[stage][lane];
 #pragma unroll
         for (uint32_t c = 0; c < (uint32_t)FAR_STAGE / 16u; c++)
           if (a0 + 16u * c < a1) cp_async16(dstage + 16u * c, out_blk + a0 + 16u * c);
-        q.far_lo = a0;
-        q.far_hi = a1 > a0 ? a1 : a0;
+        q.far = a0 | (a1 > a0 ? (a1 - a0) >> 4 : 0u);
       }
     }
     // the group's literals, one contiguous run of the literal source when
@@ -918,10 +987,10 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
       if (lit_run && l1 - l0 <= (uint32_t)LIT_STAGE) {
         const uint32_t c = l0 + 16u * lane;
         if (c < l1) cp_async16(SB.lit[stage] + (c - l0), lits + c);
-        q.lit_lo = l0;
-        q.lit_staged = true;
+        q.lit = l0 | 1u;
       }
     }
+    q.lit |= (uint32_t)err << 1;
     cp_async_commit();
     return q;
   };
@@ -930,9 +999,9 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
   Prep cur = prep(0, r_next, 0, 0, true, 0);
   r_next = load_rec(32 + lane);
   for (uint32_t g = 0; g < n_groups_total; g++) {
-    if (cur.err) {
+    if (cur.lit & 14u) {
       cp_async_wait_all();
-      if (lane == 0) set_status(status, cur.err);
+      if (lane == 0) set_status(status, (int)((cur.lit >> 1) & 7u));
       return;
     }
     const int stage = (int)(g & 1u);
@@ -947,8 +1016,11 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
     __syncwarp();
     GMP_TSTAMP(tg2);
     GMP_TADD(1, tg1, tg2);
-    const uint32_t ll = cur.ll, ml = cur.ml, dst = cur.dst, lsrc = cur.lsrc, wpos = cur.wpos, rpos = cur.rpos;
-    const bool pending = cur.valid && ml > 0;
+    const uint32_t ll = cur.ll, ml = cur.w & 0xffu, dst = cur.dst, lsrc = cur.lsrc, wpos = dst + ll,
+                   rpos = wpos - (cur.w >> 8);
+    const bool pending = ml > 0;  // lanes past the block's end have no match
+    const bool lit_staged = cur.lit & 1u;
+    const uint32_t lit_lo = cur.lit & ~15u, far_lo = cur.far & ~15u, far_hi = far_lo + 16u * (cur.far & 15u);
     const uint32_t G1 = G0 + cur.gtot;
     int rounds;
     if (fast) {
@@ -957,8 +1029,19 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
       // has room for the reads past a string's end; other sources are read
       // only up to it)
       if (cur.glits) {
-        if (cur.lit_staged) {
-          const uint8_t* ls = SB.lit[stage] + (lsrc - cur.lit_lo);
+        if (lit_staged && (dst & RING_MASK) + ll <= (uint32_t)RING) {
+          // the literal string does not cross the ring's end: base + offset
+          const uint8_t* ls = SB.lit[stage] + (lsrc - lit_lo);
+          uint8_t* rd = ring + (dst & RING_MASK);
+          for (uint32_t i = 0; i < ll; i += 4) {
+            const uint8_t b0 = ls[i], b1 = ls[i + 1], b2 = ls[i + 2], b3 = ls[i + 3];
+            rd[i] = b0;
+            if (i + 1 < ll) rd[i + 1] = b1;
+            if (i + 2 < ll) rd[i + 2] = b2;
+            if (i + 3 < ll) rd[i + 3] = b3;
+          }
+        } else if (lit_staged) {
+          const uint8_t* ls = SB.lit[stage] + (lsrc - lit_lo);
           for (uint32_t i = 0; i < ll; i += 4) {
             const uint8_t b0 = ls[i], b1 = ls[i + 1], b2 = ls[i + 2], b3 = ls[i + 3];
             ring[(dst + i) & RING_MASK] = b0;
@@ -973,14 +1056,17 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
       __syncwarp();
       GMP_TSTAMP(tg3);
       GMP_TADD(2, tg2, tg3);
-      const SrcView sv{ring, SB.far[stage][lane], out_blk, ring_lo, cur.far_lo, cur.far_hi};
+      const SrcView sv{ring, SB.far[stage][lane], out_blk, ring_lo, far_lo, far_hi};
       // DE: every source below the group start passes at once; otherwise the
       // exact per-group check decides (de_group_ok); a group that fails it is
       // resolved by MRR
       const bool de_ok = de && P.resolve == 0 &&
                          (__all_sync(FULL, !pending || rpos + ml <= G0) || de_group_ok(rpos, wpos, ml));
       if (de_ok) {
-        if (pending) copy_match_words(ring, sv, rpos, wpos, ml);
+        if (pending) {
+          if (LLB == LUT_BITS) copy_match_linear(ring, sv, rpos, wpos, ml);
+          else copy_match_words(ring, sv, rpos, wpos, ml);
+        }
         __syncwarp();
         rounds = __ballot_sync(FULL, pending) ? 1 : 0;
         if (rstat) note_round(rstat, 0, pending ? ml : 0u);
@@ -1000,7 +1086,8 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
           const uint32_t hwm = __shfl_sync(FULL, wpos, __ffs(votes) - 1);
           const bool go = pend && min(rpos + ml, wpos) <= hwm;
           if (go) {
-            copy_match_words(ring, sv, rpos, wpos, ml);
+            if (LLB == LUT_BITS) copy_match_linear(ring, sv, rpos, wpos, ml);
+            else copy_match_words(ring, sv, rpos, wpos, ml);
             pend = false;
           }
           if (rstat) note_round(rstat, rounds, go ? ml : 0u);
