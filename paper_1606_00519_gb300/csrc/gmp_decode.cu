@@ -152,6 +152,13 @@ struct KParams {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// Two 16-byte records as one 32-byte store (p 32-byte aligned).
+__device__ __forceinline__ void st_global_32B(void* p, const uint4& a, const uint4& b) {
+  asm volatile("st.global.v8.u32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z),
+               "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
+}
+
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
 __device__ __forceinline__ uint32_t ld_u32_nc(const uint8_t* p) { return __ldg(reinterpret_cast<const uint32_t*>(p)); }
@@ -701,8 +708,20 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
     for (uint32_t jb = 0; jb < K; jb += 32) {
       const uint32_t j = jb + lane;
       bool act = j < K;
-      uint32_t pos = 0, end = 0, outp = 0, out_end = 0, lit_dst = 0, lit_lim = 0, nlit = 0, q = 0, q_end = 0;
+      uint32_t pos = 0, end = 0, outp = 0, out_end = 0, lit_dst = 0, nlit = 0, q = 0, q_end = 0;
       uint32_t lit_run = 0;
+      // literal bytes of the lane, gathered eight at a time and stored as one
+      // aligned 8-byte word (lit_dst is 16-byte aligned): 32 lanes storing
+      // single bytes to 32 places cost a memory request each
+      unsigned long long lacc = 0;
+      uint32_t lit_end8 = 0;
+      // records likewise go out two at a time (32 bytes, one sector) in the
+      // 96-register instance: a record with an even index waits in `held` for
+      // the next one (in the 128-register instance, whose launches hold fewer
+      // warps, the pairing's extra instructions cost more than it saves)
+      constexpr bool PAIR_RECORDS = LLB != LUT_BITS;
+      uint4 held = make_uint4(0, 0, 0, 0);
+      bool holding = false;
       // bit buffer (nb valid bits), a stash of up to 4 words (lo, hi) and the
       // next 16-byte chunk, loaded one chunk ahead of use
       uint64_t buf = 0, lo = 0, hi = 0;
@@ -744,7 +763,9 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
         outp = S.u.a.sb_out[j];
         out_end = outp + S.u.a.sb_outn[j];
         lit_dst = ((S.u.a.sb_out[j] + 15u) & ~15u) + 16u * j;
-        lit_lim = lit_dst + S.u.a.sb_outn[j];  // first byte past the lane's literal region
+        // end of the lane's literal region, rounded up to the 8-byte words it
+        // is stored in (the next lane's region starts at or after it)
+        lit_end8 = lit_dst + ((S.u.a.sb_outn[j] + 7u) & ~7u);
         q = S.u.a.sb_seq[j];
         q_end = q + S.u.a.sb_seqn[j];
         act = q < q_end;
@@ -772,7 +793,13 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
           nb -= (int)L;
           pos += L;
           if (sym < 256) {
-            shadow[min(lit_dst + nlit, lit_lim)] = (uint8_t)sym;  // clamped: a corrupt stream is caught below
+            lacc |= (unsigned long long)sym << (8u * (nlit & 7u));
+            if ((nlit & 7u) == 7u) {
+              const uint32_t c = lit_dst + (nlit & ~7u);
+              // past the region only on a corrupt stream (caught below)
+              if (c + 8u <= lit_end8) *reinterpret_cast<unsigned long long*>(shadow + c) = lacc;
+              lacc = 0;
+            }
             nlit++;
             lit_run++;
             outp++;
@@ -802,7 +829,19 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
             }
             // the record carries the sequence's output position and literal
             // source, so that the LZ77 phase needs no prefix sums for it
-            rec[q] = make_uint4(outp - lit_run, lit_dst + nlit - lit_run, lit_run, (dist << 8) | ml);
+            {
+              const uint4 r = make_uint4(outp - lit_run, lit_dst + nlit - lit_run, lit_run, (dist << 8) | ml);
+              if (!PAIR_RECORDS) {
+                rec[q] = r;
+              } else if (q & 1u) {
+                if (holding) st_global_32B(rec + (q - 1), held, r);
+                else rec[q] = r;
+                holding = false;
+              } else {
+                held = r;
+                holding = true;
+              }
+            }
             q++;
             lit_run = 0;
             outp += ml;
@@ -826,7 +865,13 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
           nb -= (int)L;
           pos += L;
           if (sym < 256) {
-            shadow[min(lit_dst + nlit, lit_lim)] = (uint8_t)sym;  // clamped: a corrupt stream is caught below
+            lacc |= (unsigned long long)sym << (8u * (nlit & 7u));
+            if ((nlit & 7u) == 7u) {
+              const uint32_t c = lit_dst + (nlit & ~7u);
+              // past the region only on a corrupt stream (caught below)
+              if (c + 8u <= lit_end8) *reinterpret_cast<unsigned long long*>(shadow + c) = lacc;
+              lacc = 0;
+            }
             nlit++;
             lit_run++;
             outp++;
@@ -856,7 +901,19 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
             }
             // the record carries the sequence's output position and literal
             // source, so that the LZ77 phase needs no prefix sums for it
-            rec[q] = make_uint4(outp - lit_run, lit_dst + nlit - lit_run, lit_run, (dist << 8) | ml);
+            {
+              const uint4 r = make_uint4(outp - lit_run, lit_dst + nlit - lit_run, lit_run, (dist << 8) | ml);
+              if (!PAIR_RECORDS) {
+                rec[q] = r;
+              } else if (q & 1u) {
+                if (holding) st_global_32B(rec + (q - 1), held, r);
+                else rec[q] = r;
+                holding = false;
+              } else {
+                held = r;
+                holding = true;
+              }
+            }
             q++;
             lit_run = 0;
             outp += ml;
@@ -870,6 +927,12 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
         __syncwarp();
       }
       if (j < K) {
+        if (holding) rec[q - 1] = held;  // the lane's last record, alone
+        // the last, partial word of literals
+        if (nlit & 7u) {
+          const uint32_t c = lit_dst + (nlit & ~7u);
+          if (c + 8u <= lit_end8) *reinterpret_cast<unsigned long long*>(shadow + c) = lacc;
+        }
         if (!err && pos != end) err = GMP_STATUS_BITSTREAM;
         if (!err && outp != out_end) err = GMP_STATUS_OUTPUT_OVERRUN;
       }
