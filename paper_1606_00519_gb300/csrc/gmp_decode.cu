@@ -15,7 +15,9 @@
 //  sequences as 16-byte records {output position, literal source, literal
 //  length, (distance << 8) | match length} and its literal bytes to the
 //  warp's scratch slot (device memory, as in the paper, where the decoder's
-//  token stream goes to device memory).  The lane knows each sequence's
+//  token stream goes to device memory): literals eight at a time, records
+//  (in the 96-register instance) two at a time, since every store of the 32
+//  lanes to 32 places costs a memory request per lane.  The lane knows each sequence's
 //  output position and literal source as it decodes it, so the records carry
 //  the results of the two prefix sums of Sec. 3.2.2.
 //
@@ -728,6 +730,23 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
       int nb = 0;
       uint32_t scnt = 0, ci = 0;
       uint4 pre = make_uint4(0, 0, 0, 0);
+      // refill before a literal/length code, the common part without a
+      // branch: the stash is reloaded first if it is empty (every fourth word)
+      auto refill_ll = [&]() {
+        if (scnt == 0) {
+          lo = (uint64_t)pre.x | ((uint64_t)pre.y << 32);
+          hi = (uint64_t)pre.z | ((uint64_t)pre.w << 32);
+          scnt = 4;
+          pre = ld4(ci++);
+        }
+        const bool need = nb <= 32;
+        buf |= (uint64_t)(need ? (uint32_t)lo : 0u) << (nb & 63);
+        nb += need ? 32 : 0;
+        const uint64_t lo2 = (lo >> 32) | (hi << 32), hi2 = hi >> 32;
+        lo = need ? lo2 : lo;
+        hi = need ? hi2 : hi;
+        scnt -= need ? 1u : 0u;
+      };
       auto next_word = [&]() -> uint32_t {
         if (scnt == 0) {
           lo = (uint64_t)pre.x | ((uint64_t)pre.y << 32);
@@ -781,10 +800,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
         // two symbols per lane per warp step (the second only if the lane is
         // still active), halving the votes and reconvergence points
         if (act) {
-          if (nb <= 32) {
-            buf |= (uint64_t)next_word() << nb;
-            nb += 32;
-          }
+          refill_ll();
           uint32_t e = S.u.a.ll[buf & ((1u << LLB) - 1u)];
           if (LLB < LUT_BITS && e == LONG_CODE)
             e = decode_long<LLB>(S.u.a.cll, S.u.a.sorted_ll, (uint32_t)buf & (LUT_SIZE - 1));
@@ -853,10 +869,7 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
           act = !err && q < q_end;
         }
         if (act) {  // second symbol of the step
-          if (nb <= 32) {
-            buf |= (uint64_t)next_word() << nb;
-            nb += 32;
-          }
+          refill_ll();
           uint32_t e = S.u.a.ll[buf & ((1u << LLB) - 1u)];
           if (LLB < LUT_BITS && e == LONG_CODE)
             e = decode_long<LLB>(S.u.a.cll, S.u.a.sorted_ll, (uint32_t)buf & (LUT_SIZE - 1));
