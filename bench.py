@@ -340,7 +340,7 @@ def measure_decode(args, w, data, streams, dev, dist=None, rank=0, clocks=False,
     ds = {m: gmp.DeviceStream(streams[m], device=dev) for m in modes}
     outs = {m: torch.empty(data.size, dtype=torch.uint8, device=dev) for m in modes}
     ctx = gmp.Context(device=local, max_block_out=w.block_size, warps_per_cta=args.warps_per_cta,
-                      collect_stats=False)
+                      ctas_per_sm=args.ctas_per_sm, collect_stats=False)
     table = gmp.make_file_table([ds[m].file_desc(outs[m]) for m in modes], device=dev)
     status = torch.zeros(len(modes), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -350,7 +350,7 @@ def measure_decode(args, w, data, streams, dev, dist=None, rank=0, clocks=False,
     if not args.warps_per_cta:
         tuned = ctx.autotune(table, len(modes), status, stream)
     shape = {"warps_per_cta": tuned["warps_per_cta"] if tuned else args.warps_per_cta,
-             "ctas_per_sm": tuned["ctas_per_sm"] if tuned else 0, "autotuned": tuned is not None}
+             "ctas_per_sm": tuned["ctas_per_sm"] if tuned else args.ctas_per_sm, "autotuned": tuned is not None}
     out_bytes = data.size * len(modes)
     comp_bytes = sum(ds[m].comp_bytes for m in modes)
 
@@ -964,7 +964,8 @@ def main():
     ap.add_argument("--size", type=int, default=None, help="override bytes per stream")
     ap.add_argument("--format", default="bit", choices=["bit", "byte"],
                     help="stream format: Huffman blocks (bit) or byte-level blocks (byte)")
-    ap.add_argument("--warps-per-cta", type=int, default=0)
+    ap.add_argument("--warps-per-cta", type=int, default=0, help="fixed launch shape instead of the autotuner's")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="with --warps-per-cta: CTAs per SM (0: as many as fit)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU baseline")
     ap.add_argument("--ref-blocks", type=int, default=16, help="oracle blocks per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
