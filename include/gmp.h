@@ -113,7 +113,9 @@ typedef enum {
   GMP_STATUS_BAD_OFFSET = 4,        /* distance 0, beyond the window, or before the block start */
   GMP_STATUS_OUTPUT_OVERRUN = 5,    /* decoded sizes disagree with the header or exceed out_cap */
   GMP_STATUS_MRR_NO_PROGRESS = 6,   /* a resolution round made no progress (cannot happen on valid input) */
-  GMP_STATUS_CAPACITY = 7           /* a block needs more scratch than the context reserved */
+  GMP_STATUS_CAPACITY = 7,          /* a block needs more scratch than the context reserved */
+  GMP_STATUS_INPUT_TIMEOUT = 8      /* host-to-host calls: a piece's input copy did not complete within the
+                                       kernel's wait limit (about 10 s); its blocks were not decoded */
 } gmp_status;
 
 /* ------------------------------------------------------------------------ */
@@ -338,15 +340,20 @@ int gmp_stats_read(gmp_context* ctx, gmp_stats* out); /* synchronises the device
 
 /* ------------------------------------------------------------------------ */
 /* Host-to-host decompression (the paper's "(In/Out)" mode, Sec. 5.4: input
-   and output in host memory, transfers included).  The streams' blocks are
-   cut into pieces, one persistent launch each, run on up to 8 partitions of
-   the context's scratch, each with its own CUDA streams for the copy in,
-   the launch and the copy back: a piece's input copy overlaps the decoding
-   of other pieces, and its output is copied back as soon as its launch
-   ends, while other pieces still decode.  Host buffers
-   should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to
-   overlap; pageable buffers work but serialise the copies.  Uses (and grows)
-   device staging buffers owned by the context.
+   and output in host memory, transfers included).  One persistent launch
+   decodes all the streams' blocks, which are cut into pieces of consecutive
+   blocks (about 32 pieces, 8 to 256 blocks each).  The pieces are copied in,
+   in order, on one copy stream, which sets a device flag after each piece;
+   a warp waits for its piece's flag before reading it, so decoding starts
+   with the first piece.  The kernel sets a second flag once a piece is
+   decoded, and the piece's copy back waits for that flag (a stream memory
+   operation, cuStreamWaitValue32) on one of 8 copy-back streams, so outputs
+   go back while later pieces decode.  A warp's wait for its input is bounded
+   (about 10 s; then the file's status is GMP_STATUS_INPUT_TIMEOUT), so the
+   call always ends.  Host buffers should be pinned (cudaHostAlloc /
+   cudaHostRegister) for the copies to overlap; pageable buffers work but
+   serialise the copies.  Uses (and grows) device staging buffers owned by
+   the context.  GMP_ERR_CUDA if the driver lacks stream memory operations.
    gmp_decompress_host_batch: n_files streams (host_streams[f], bytes[f]) into
    host_outs[f] (out_caps[f] bytes each); statuses[f] (host) receives file
    f's decoder status.  GMP_ERR_CAPACITY if an output buffer is too small or
@@ -362,7 +369,7 @@ int gmp_decompress_host(gmp_context* ctx, const void* host_stream, size_t bytes,
 /* The paper's "(In)" mode (Sec. 5.4: compressed input in host memory, the
    decompressed output left on the GPU): as gmp_decompress_host_batch, but
    d_outs[f] are device buffers of the context's device (out_caps[f] bytes
-   each), which the pieces decode into directly; there are no copies back.
+   each), which the launch decodes into directly; there are no copies back.
    The input copies overlap the decoding of earlier pieces.  Synchronous in
    the same way (returns with every output in device memory and statuses[f]
    filled in on the host). */

@@ -27,7 +27,7 @@ from ._native import (BlockRef, Completion, CompressOpts, ContextOpts, FileDesc,
 OK = 0
 RESOLVE = {"auto": 0, "mrr": 1, "sc": 2}
 STATUS_NAMES = {0: "OK", 1: "BAD_HEADER", 2: "CORRUPT_SYMBOL", 3: "BITSTREAM", 4: "BAD_OFFSET",
-                5: "OUTPUT_OVERRUN", 6: "MRR_NO_PROGRESS", 7: "CAPACITY"}
+                5: "OUTPUT_OVERRUN", 6: "MRR_NO_PROGRESS", 7: "CAPACITY", 8: "INPUT_TIMEOUT"}
 ERROR_NAMES = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "CUDA", -4: "UNSUPPORTED", -5: "FORMAT", -6: "NOMEM"}
 
 

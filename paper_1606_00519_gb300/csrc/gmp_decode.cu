@@ -150,6 +150,17 @@ struct KParams {
   int collect_stats;
   int resolve;  // 0: by the stream's DE flag, 1: MRR always, 2: sequential copying (SC)
   int spread;   // 1: first items fixed and interleaved over the CTAs; 0: all from the counter
+  // Host-to-host pipeline (all null otherwise): a file's input is complete
+  // once in_ready[file] reaches gen (written by the copy stream after the
+  // copy); out_ready[file] is set to gen once all its blocks are decoded
+  // (done[file] counts them), and by the last warp to exit (exited counts
+  // the warps) for every file.
+  const uint32_t* in_ready;
+  uint32_t* abort_wait;  // set once a wait has run out: later waits give up at once
+  uint32_t* out_ready;
+  uint32_t* done;
+  uint32_t* exited;
+  uint32_t gen;
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -162,6 +173,89 @@ __device__ __forceinline__ void st_global_32B(void* p, const uint4& a, const uin
 }
 
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
+
+// ---- host-to-host pipeline flags
+// The wait for a file's input is bounded: about 10 s of the global timer, and
+// at most 2^24 polls; past that the file gets GMP_STATUS_INPUT_TIMEOUT, its
+// blocks are skipped and every later wait of the launch gives up at once, so
+// the launch always ends.
+constexpr unsigned long long kInputWaitNs = 10000000000ull;
+constexpr uint32_t kInputWaitPolls = 1u << 24;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Whole warp: true once *flag has reached gen (cyclic comparison, as the
+// copy stream's flag values wrap), false if the wait ran out.  The warp polls
+// and sleeps as one: with lane 0 polling and sleeping alone while the other
+// lanes waited at a shuffle, the warps decoded their next blocks 2 to 2.7
+// times slower (measured on text256m, (In) mode).
+__device__ __noinline__ bool wait_input(const uint32_t* flag, uint32_t* abort_wait, uint32_t gen) {
+  const unsigned long long t0 = global_ns();
+  bool ok = false;
+  for (uint32_t i = 0; i < kInputWaitPolls; i++) {
+    // lane 0 reads the flag, the abort word and the clock; every decision
+    // below is taken on its values, so the lanes leave the loop together
+    uint32_t v = 0, stop = 0;
+    if ((threadIdx.x & 31u) == 0) {
+      v = ld_acquire_sys(flag);
+      stop = *reinterpret_cast<volatile uint32_t*>(abort_wait) != 0u || global_ns() - t0 > kInputWaitNs;
+    }
+    v = __shfl_sync(0xffffffffu, v, 0);
+    stop = __shfl_sync(0xffffffffu, stop, 0);
+    if ((int32_t)(v - gen) >= 0) {
+      ok = true;
+      break;
+    }
+    if (stop) break;
+    __nanosleep(i < 64 ? 64 : 1024);
+  }
+  if (!ok && (threadIdx.x & 31u) == 0) atomicExch(abort_wait, 1u);
+  __syncwarp();
+  return ok;
+}
+
+// Whole warp, after a block of `file` (n_blocks blocks) is decoded: every
+// lane's output stores are made visible before the block is counted, and
+// the count that completes the file publishes its out_ready flag.
+__device__ __noinline__ void block_done(uint32_t* done, uint32_t* out_ready, uint32_t gen, uint64_t n_blocks) {
+  __threadfence();
+  __syncwarp();
+  if ((threadIdx.x & 31u) == 0) {
+    const uint32_t d = atomicAdd(done, 1u) + 1u;
+    if (d == (uint32_t)n_blocks) {
+      __threadfence_system();
+      st_release_sys(out_ready, gen);
+    }
+  }
+  __syncwarp();
+}
+
+// Whole warp, on leaving the persistent loop: the last warp of the launch
+// sets every file's out_ready flag, so that no copy stream waits on a flag
+// that is never written.
+__device__ __noinline__ void pipeline_exit(uint32_t* exited, uint32_t* out_ready, uint32_t gen, uint32_t n_files,
+                                           uint32_t n_warps) {
+  __threadfence();
+  uint32_t last = 0;
+  if ((threadIdx.x & 31u) == 0) last = atomicAdd(exited, 1u) + 1u == n_warps;
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence_system();
+    for (uint32_t f = threadIdx.x & 31u; f < n_files; f += 32) st_release_sys(out_ready + f, gen);
+  }
+}
 
 __device__ __forceinline__ uint32_t ld_u32_nc(const uint8_t* p) { return __ldg(reinterpret_cast<const uint32_t*>(p)); }
 __device__ __forceinline__ uint64_t ld_u64_nc(const uint8_t* p) {
@@ -1246,8 +1340,13 @@ __device__ void decode_block(WarpSmem<LLB>& S, const KParams& P, const gmp_file_
 // warps fit per SM (more blocks in flight for inputs of many waves); the
 // other instance keeps 128 registers (16 warps per SM), which makes a single
 // block's decode faster when every block is in flight at once.
-template <bool STATS, bool DEEP>
+// PIPE: the host-to-host pipeline's flag waits and counts (the statistics
+// instances always carry them); the instances without it are the ones the
+// device-resident calls launch, whose code the flags would otherwise change
+// (0.8 % slower on csv1g in the 96-register instance).
+template <bool STATS, bool DEEP, bool PIPE>
 __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(const KParams P) {
+  constexpr bool kPipe = PIPE || STATS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
@@ -1293,12 +1392,18 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
     } else {
       F = P.single;
     }
-    decode_block<STATS, LLB>(S, P, F, b, P.status + file, slot, st_acc);
+    if (!kPipe || !P.in_ready || wait_input(P.in_ready + file, P.abort_wait, P.gen)) {
+      decode_block<STATS, LLB>(S, P, F, b, P.status + file, slot, st_acc);
+    } else if (lane == 0) {
+      set_status(P.status + file, GMP_STATUS_INPUT_TIMEOUT);
+    }
     __syncwarp();
+    if (kPipe && P.out_ready) block_done(P.done + file, P.out_ready + file, P.gen, F.n_blocks);
     unsigned long long next = 0;
     if (lane == 0) next = fixed + atomicAdd(P.counter, 1ull);
     item = __shfl_sync(FULL, next, 0);
   }
+  if (kPipe && P.out_ready) pipeline_exit(P.exited, P.out_ready, P.gen, P.files ? P.n_files : 1u, gridDim.x * (blockDim.x >> 5));
   if (STATS && lane == 0 && st_acc[3]) {
     atomicAdd(&P.stats[0], st_acc[0]);
     atomicAdd(&P.stats[1], st_acc[1]);
@@ -1379,20 +1484,22 @@ cudaError_t configure_kernel(bool deep, size_t smem_bytes) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if (deep) {
-    e = cudaFuncSetAttribute(decode_kernel<false, true>, a, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<true, true>, a, b);
+    e = cudaFuncSetAttribute(decode_kernel<false, true, false>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<false, true, true>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<true, true, true>, a, b);
   } else {
-    e = cudaFuncSetAttribute(decode_kernel<false, false>, a, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<true, false>, a, b);
+    e = cudaFuncSetAttribute(decode_kernel<false, false, false>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<false, false, true>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(decode_kernel<true, false, true>, a, b);
   }
   return e;
 }
 
 cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, bool deep, int* ctas_per_sm) {
   if (deep)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false, true>, warps_per_cta * 32,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false, true, false>, warps_per_cta * 32,
                                                          smem_bytes);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false, false>, warps_per_cta * 32,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, decode_kernel<false, false, false>, warps_per_cta * 32,
                                                        smem_bytes);
 }
 
@@ -1400,9 +1507,17 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,
                           unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,
                           uint32_t max_seq, uint32_t max_out, unsigned long long* stats, int collect_stats,
-                          int resolve, cudaStream_t stream, int spread) {
+                          int resolve, cudaStream_t stream, int spread, const PipeFlags* pipe) {
   KParams P;
   P.spread = spread;
+  P.in_ready = pipe ? pipe->in_ready : nullptr;
+  P.abort_wait = pipe ? pipe->abort_wait : nullptr;
+  P.out_ready = pipe ? pipe->out_ready : nullptr;
+  P.done = pipe ? pipe->done : nullptr;
+  P.exited = pipe ? pipe->exited : nullptr;
+  P.gen = pipe ? pipe->gen : 0u;
+  // in_ready needs the abort word, out_ready its counters
+  if ((P.in_ready && !P.abort_wait) || (P.out_ready && (!P.done || !P.exited))) return cudaErrorInvalidValue;
   P.files = files;
   P.item_start = item_start;
   P.n_files = n_files;
@@ -1423,18 +1538,21 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
   if (e != cudaSuccess) return e;
   const dim3 grid(shape.grid), block(shape.warps_per_cta * 32);
   if (collect_stats) {
-    if (deep) decode_kernel<true, true><<<grid, block, shape.smem_bytes, stream>>>(P);
-    else decode_kernel<true, false><<<grid, block, shape.smem_bytes, stream>>>(P);
+    if (deep) decode_kernel<true, true, true><<<grid, block, shape.smem_bytes, stream>>>(P);
+    else decode_kernel<true, false, true><<<grid, block, shape.smem_bytes, stream>>>(P);
+  } else if (pipe) {
+    if (deep) decode_kernel<false, true, true><<<grid, block, shape.smem_bytes, stream>>>(P);
+    else decode_kernel<false, false, true><<<grid, block, shape.smem_bytes, stream>>>(P);
   } else {
-    if (deep) decode_kernel<false, true><<<grid, block, shape.smem_bytes, stream>>>(P);
-    else decode_kernel<false, false><<<grid, block, shape.smem_bytes, stream>>>(P);
+    if (deep) decode_kernel<false, true, false><<<grid, block, shape.smem_bytes, stream>>>(P);
+    else decode_kernel<false, false, false><<<grid, block, shape.smem_bytes, stream>>>(P);
   }
   return cudaGetLastError();
 }
 
 cudaError_t kernel_arch(int* binary_version, int* ptx_version) {
   cudaFuncAttributes fa;
-  const cudaError_t e = cudaFuncGetAttributes(&fa, decode_kernel<false, false>);
+  const cudaError_t e = cudaFuncGetAttributes(&fa, decode_kernel<false, false, false>);
   if (e != cudaSuccess) return e;
   if (binary_version) *binary_version = fa.binaryVersion;
   if (ptx_version) *ptx_version = fa.ptxVersion;

@@ -1,6 +1,7 @@
 // gmp_host.cpp - host runtime of libgmp: stream header and block index,
 // decoder contexts (scratch sizing, launch shape), launches, CUDA graphs of
 // batched launches, statistics, and the host-to-host convenience call.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -47,6 +48,36 @@ struct DeviceGuard {
   }
 };
 
+// Stream memory operations of the host-to-host pipeline: a copy stream
+// writes a word once the copies before it have completed (with a memory
+// barrier first), or waits until a word reaches a value (cyclic >=).  The
+// driver functions are fetched through the runtime, so the library does not
+// link the driver library itself.
+using StreamValueFn = CUresult (*)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+struct StreamValueOps {
+  StreamValueFn write = nullptr, wait = nullptr;
+};
+const StreamValueOps* stream_value_ops() {
+  static StreamValueOps ops;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* w = nullptr;
+    void* t = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &w, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuStreamWaitValue32", &t, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && w && t) {
+      ops.write = reinterpret_cast<StreamValueFn>(w);
+      ops.wait = reinterpret_cast<StreamValueFn>(t);
+    }
+  });
+  return ops.write ? &ops : nullptr;
+}
+int cu_fail(CUresult r, const char* what) {
+  g_cuda_err = std::string(what) + ": CUresult " + std::to_string((int)r);
+  return GMP_ERR_CUDA;
+}
+
 }  // namespace
 
 namespace gmp {
@@ -71,16 +102,23 @@ struct gmp_context {
   size_t h_comp_cap = 0;
   uint8_t* h_out = nullptr;
   size_t h_out_cap = 0;
-  gmp_block_ref* h_index = nullptr;
-  size_t h_index_cap = 0;
+  uint8_t* h_meta = nullptr;  // block indexes, piece descriptors, item prefix
+  size_t h_meta_cap = 0;
   int32_t* h_status = nullptr;
   size_t h_status_cap = 0;
-  // pipeline of the host-to-host calls: one stream per scratch partition,
-  // one stream for the copies back, and events between them
-  cudaStream_t pipe[gmp::kPipeParts] = {};
-  cudaStream_t h2d[gmp::kPipeParts] = {};
+  // flags of the host-to-host launch: in_ready, out_ready and done, h_flags_n
+  // words each, then the exited-warps word; in_ready and out_ready keep the
+  // generation numbers of earlier calls (pipe_gen)
+  uint32_t* h_flags = nullptr;
+  size_t h_flags_n = 0;
+  uint32_t pipe_gen = 0;
+  // streams of the host-to-host calls: the launch, the copies in, the copies
+  // back (several, so that a piece whose copy waits does not hold up the
+  // others), and events between them
+  cudaStream_t pipe = nullptr;
+  cudaStream_t h2d = nullptr;
   cudaStream_t d2h[gmp::kPipeParts] = {};
-  std::vector<cudaEvent_t> events;
+  cudaEvent_t ev[2] = {};
 };
 
 struct gmp_graph {
@@ -259,15 +297,15 @@ void gmp_context_destroy(gmp_context* c) {
   if (c->item_start) cudaFree(c->item_start);
   if (c->h_comp) cudaFree(c->h_comp);
   if (c->h_out) cudaFree(c->h_out);
-  if (c->h_index) cudaFree(c->h_index);
+  if (c->h_meta) cudaFree(c->h_meta);
   if (c->h_status) cudaFree(c->h_status);
-  for (cudaStream_t t : c->pipe)
-    if (t) cudaStreamDestroy(t);
+  if (c->h_flags) cudaFree(c->h_flags);
+  if (c->pipe) cudaStreamDestroy(c->pipe);
+  if (c->h2d) cudaStreamDestroy(c->h2d);
   for (cudaStream_t t : c->d2h)
     if (t) cudaStreamDestroy(t);
-  for (cudaStream_t t : c->h2d)
-    if (t) cudaStreamDestroy(t);
-  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 
@@ -475,6 +513,23 @@ int gmp_stats_read(gmp_context* c, gmp_stats* out) {
 // Host streams in; outputs in host memory (to_device false: decoded into the
 // context's device staging and copied back piece by piece) or in device
 // memory (to_device true: decoded straight into the caller's buffers).
+//
+// One persistent launch decodes every block of every stream.  The blocks are
+// cut into pieces (runs of consecutive blocks of one stream), which are the
+// files of that launch.  The pieces' compressed bytes are copied in, in
+// piece order, on one copy stream; after each copy the stream sets the
+// piece's in_ready word, and a warp waits (bounded) for that word before it
+// reads any byte of the piece, so the decoding starts with the first piece.
+// The kernel sets a piece's out_ready word once all its blocks are decoded,
+// and the piece's copy back waits for that word on one of the copy-back
+// streams, so outputs go back while later pieces still decode.
+//
+// A piece's copy in runs on to the next 128-byte boundary of the staging
+// (into the next piece's bytes, which that piece's copy writes again with the
+// same values), and each stream's staging starts on a 128-byte boundary: the
+// cache lines a piece's blocks share with a later piece are then complete
+// when the piece is flagged, so no SM caches a line before all of its bytes
+// have arrived.
 static int decompress_from_host(gmp_context* c, size_t n_files, const void* const* host_streams, const size_t* bytes,
                                 void* const* outs, const size_t* out_caps, int32_t* statuses, void* stream,
                                 bool to_device) {
@@ -482,6 +537,8 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
   if (!c || (n_files && (!host_streams || !bytes || !host_outs || !out_caps || !statuses))) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const StreamValueOps* ops = stream_value_ops();
+  if (!ops) return cuda_fail(cudaErrorNotSupported, "cuStreamWriteValue32 / cuStreamWaitValue32 entry points");
   // ---- parse every stream; lay out the device staging
   struct File {
     std::vector<gmp_block_ref> idx;
@@ -504,26 +561,19 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
       files[f].comp_off = comp_total;
       files[f].out_off = out_total;
       files[f].idx_off = n_total;
-      comp_total += (bytes[f] + 15) & ~uint64_t(15);
+      comp_total += (bytes[f] + 127) & ~uint64_t(127);
       out_total += (files[f].info.orig_size + 15) & ~uint64_t(15);
       n_total += nb;
     }
   } catch (...) {
     return GMP_ERR_NOMEM;
   }
-  // ---- pieces: runs of consecutive blocks of one stream, one launch each.
-  // The scratch's warp slots are cut into kPipeParts partitions; piece j runs
-  // on partition j % kPipeParts (its own stream, work counter and slots), so
-  // up to kPipeParts pieces decode at once and a piece's copy back starts as
-  // soon as its launch ends.  A piece holds at most one partition's warps of
-  // blocks, so each launch is one wave.
-  const uint64_t wpc = (uint64_t)c->shape.warps_per_cta;
-  const uint64_t slots = (uint64_t)c->shape.grid * wpc;
-  uint64_t parts = gmp::kPipeParts;
-  while (parts > 1 && slots / parts < wpc) parts--;
-  const uint64_t part_warps = slots / parts / wpc * wpc;
-  const uint64_t piece_blocks =
-      std::max<uint64_t>(1, std::min<uint64_t>((n_total + parts - 1) / parts, part_warps));
+  // ---- pieces: about kPieces of them, of kPieceMin to kPieceMax blocks.
+  // Each piece's copy in ends with a flag write, whose memory barrier keeps
+  // the next copy from starting at once: with 128 pieces the copies in of a
+  // 0.66 GB input took 4.3-5.9 ms, with 32 about 3.7 ms.
+  constexpr uint64_t kPieces = 32, kPieceMin = 8, kPieceMax = 256;
+  const uint64_t piece_blocks = std::min(kPieceMax, std::max(kPieceMin, (n_total + kPieces - 1) / kPieces));
   struct Piece {
     size_t file;
     uint64_t b0, b1;
@@ -537,7 +587,15 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
     return GMP_ERR_NOMEM;
   }
   const size_t n_pieces = pieces.size();
-  // ---- staging buffers, streams and events (kept in the context)
+  for (size_t f = 0; f < n_files; f++) statuses[f] = 0;
+  if (n_pieces == 0) return GMP_OK;  // only empty streams
+  if (n_pieces > (size_t)INT32_MAX) return GMP_ERR_CAPACITY;
+  // ---- device buffers (kept in the context): staging, metadata (block
+  // indexes, one descriptor per piece, the work-item prefix over the pieces),
+  // statuses and flags
+  const size_t desc_off = (n_total * sizeof(gmp_block_ref) + 63) & ~size_t(63);
+  const size_t pre_off = desc_off + ((n_pieces * sizeof(gmp_file_desc) + 63) & ~size_t(63));
+  const size_t meta_bytes = pre_off + (n_pieces + 1) * sizeof(uint64_t);
   auto grow = [&](auto** p, size_t* cap, size_t need) -> int {
     if (*cap >= need) return GMP_OK;
     if (*p) cudaFree(*p);
@@ -548,85 +606,150 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
     return GMP_OK;
   };
   int rc;
-  if ((rc = grow(&c->h_comp, &c->h_comp_cap, std::max<uint64_t>(comp_total, 16)))) return rc;
+  if ((rc = grow(&c->h_comp, &c->h_comp_cap, comp_total))) return rc;
   if (!to_device && (rc = grow(&c->h_out, &c->h_out_cap, std::max<uint64_t>(out_total, 16)))) return rc;
-  if ((rc = grow(&c->h_index, &c->h_index_cap, std::max<uint64_t>(n_total, 1) * sizeof(gmp_block_ref)))) return rc;
-  if ((rc = grow(&c->h_status, &c->h_status_cap, std::max<size_t>(n_pieces, 1) * sizeof(int32_t)))) return rc;
-  for (uint64_t k = 0; k < parts; k++) {
-    if (!c->pipe[k]) GMP_CUDA(cudaStreamCreateWithFlags(&c->pipe[k], cudaStreamNonBlocking));
+  if ((rc = grow(&c->h_meta, &c->h_meta_cap, meta_bytes))) return rc;
+  if ((rc = grow(&c->h_status, &c->h_status_cap, n_pieces * sizeof(int32_t)))) return rc;
+  if (c->h_flags_n < n_pieces) {
+    if (c->h_flags) cudaFree(c->h_flags);
+    c->h_flags = nullptr;
+    c->h_flags_n = 0;
+    const size_t n = std::max<size_t>(n_pieces, 1024);
+    GMP_CUDA(cudaMalloc((void**)&c->h_flags, (3 * n + 2) * sizeof(uint32_t)));
+    GMP_CUDA(cudaMemset(c->h_flags, 0, (3 * n + 2) * sizeof(uint32_t)));
+    c->h_flags_n = n;
+  }
+  if (!c->pipe) GMP_CUDA(cudaStreamCreateWithFlags(&c->pipe, cudaStreamNonBlocking));
+  if (!c->h2d) GMP_CUDA(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking));
+  for (uint32_t k = 0; k < gmp::kPipeParts; k++)
     if (!c->d2h[k]) GMP_CUDA(cudaStreamCreateWithFlags(&c->d2h[k], cudaStreamNonBlocking));
-    if (!c->h2d[k]) GMP_CUDA(cudaStreamCreateWithFlags(&c->h2d[k], cudaStreamNonBlocking));
+  for (cudaEvent_t& e : c->ev)
+    if (!e) GMP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  const size_t fn = c->h_flags_n;
+  uint32_t* in_ready = c->h_flags;
+  uint32_t* out_ready = c->h_flags + fn;
+  uint32_t* done = c->h_flags + 2 * fn;  // then the exited-warps word and the abort word
+  // Generation of this call: the flags of earlier calls hold smaller ones
+  // (compared cyclically); restarted from 1, with the flags cleared, long
+  // before the comparison could wrap.
+  if (c->pipe_gen >= (1u << 30)) {
+    GMP_CUDA(cudaMemsetAsync(c->h_flags, 0, 2 * fn * sizeof(uint32_t), s));
+    c->pipe_gen = 0;
   }
-  while (c->events.size() < 2 * n_pieces + 2) {
-    cudaEvent_t e;
-    GMP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    c->events.push_back(e);
+  const uint32_t gen = ++c->pipe_gen;
+  // ---- metadata, assembled on the host and copied in once
+  std::vector<uint8_t> meta;
+  try {
+    meta.assign(meta_bytes, 0);
+  } catch (...) {
+    return GMP_ERR_NOMEM;
   }
-  // ---- enqueue: block indexes and the streams' headers (on the caller's
-  // stream), then per piece its blocks' bytes (on its partition's copy-in
-  // stream) and its launch (on its partition's stream) ...
-  cudaEvent_t e_start = c->events[2 * n_pieces], e_end = c->events[2 * n_pieces + 1];
+  gmp_block_ref* m_idx = reinterpret_cast<gmp_block_ref*>(meta.data());
+  gmp_file_desc* m_desc = reinterpret_cast<gmp_file_desc*>(meta.data() + desc_off);
+  uint64_t* m_pre = reinterpret_cast<uint64_t*>(meta.data() + pre_off);
+  const gmp_block_ref* d_idx = reinterpret_cast<const gmp_block_ref*>(c->h_meta);
+  for (size_t f = 0; f < n_files; f++)
+    if (!files[f].idx.empty())
+      memcpy(m_idx + files[f].idx_off, files[f].idx.data(), files[f].idx.size() * sizeof(gmp_block_ref));
+  uint64_t items = 0;
+  for (size_t j = 0; j < n_pieces; j++) {
+    const Piece& q = pieces[j];
+    const File& F = files[q.file];
+    uint8_t* dec_out = to_device ? static_cast<uint8_t*>(outs[q.file]) : c->h_out + F.out_off;
+    m_desc[j] = gmp_file_desc{c->h_comp + F.comp_off, bytes[q.file], d_idx + F.idx_off + q.b0, q.b1 - q.b0, dec_out,
+                              F.info.orig_size};
+    m_pre[j] = items;
+    items += q.b1 - q.b0;
+  }
+  m_pre[n_pieces] = items;
+  // ---- on the caller's stream: metadata, stream headers (with the block
+  // offset tables), zeroed statuses, block counts, exit word and work counter
+  unsigned long long* counter = c->counter + 48;
+  GMP_CUDA(cudaMemcpyAsync(c->h_meta, meta.data(), meta_bytes, cudaMemcpyHostToDevice, s));
   for (size_t f = 0; f < n_files; f++) {
     if (files[f].idx.empty()) continue;
-    GMP_CUDA(cudaMemcpyAsync(c->h_index + files[f].idx_off, files[f].idx.data(),
-                             files[f].idx.size() * sizeof(gmp_block_ref), cudaMemcpyHostToDevice, s));
     GMP_CUDA(cudaMemcpyAsync(c->h_comp + files[f].comp_off, host_streams[f], files[f].idx[0].comp_offset,
                              cudaMemcpyHostToDevice, s));
   }
-  GMP_CUDA(cudaEventRecord(e_start, s));
-  for (uint64_t k = 0; k < parts; k++) GMP_CUDA(cudaStreamWaitEvent(c->h2d[k], e_start, 0));
-  for (size_t j = 0; j < n_pieces; j++) {
+  GMP_CUDA(cudaMemsetAsync(c->h_status, 0, n_pieces * sizeof(int32_t), s));
+  GMP_CUDA(cudaMemsetAsync(done, 0, (fn + 2) * sizeof(uint32_t), s));
+  GMP_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+  GMP_CUDA(cudaEventRecord(c->ev[0], s));
+  // ---- the launch first: the copy streams' waits below are then queued
+  // after it, so it never waits behind them
+  GMP_CUDA(cudaStreamWaitEvent(c->pipe, c->ev[0], 0));
+  const gmp::PipeFlags pf{in_ready, done + fn + 1, to_device ? nullptr : out_ready, to_device ? nullptr : done,
+                          to_device ? nullptr : done + fn, gen};
+  GMP_CUDA(gmp::launch_decode(c->shape, reinterpret_cast<const gmp_file_desc*>(c->h_meta + desc_off),
+                              reinterpret_cast<const uint64_t*>(c->h_meta + pre_off), (uint32_t)n_pieces, nullptr,
+                              c->h_status, counter, c->scratch, c->slot_bytes, c->shadow_off, c->max_seq, c->max_out,
+                              c->stats, (int)c->opts.collect_stats, (int)c->opts.resolve, c->pipe, 1, &pf));
+  // From here on the launch runs: a failure below still waits for it (its
+  // waits for missing pieces end by themselves) before returning.
+  rc = GMP_OK;
+  cudaError_t ce = cudaStreamWaitEvent(c->h2d, c->ev[0], 0);
+  if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaStreamWaitEvent");
+  // ---- the copies in, in piece order, each followed by its piece's flag
+  for (size_t j = 0; j < n_pieces && rc == GMP_OK; j++) {
     const Piece& q = pieces[j];
     const File& F = files[q.file];
     const uint8_t* src = static_cast<const uint8_t*>(host_streams[q.file]);
     const uint64_t c0 = F.idx[q.b0].comp_offset;
     const uint64_t c1 = q.b1 == F.idx.size() ? bytes[q.file] : F.idx[q.b1].comp_offset;
-    cudaStream_t in_s = c->h2d[j % parts];
-    GMP_CUDA(cudaMemcpyAsync(c->h_comp + F.comp_off + c0, src + c0, c1 - c0, cudaMemcpyHostToDevice, in_s));
-    GMP_CUDA(cudaEventRecord(c->events[2 * j], in_s));
-    const uint64_t k = j % parts;
-    cudaStream_t t = c->pipe[k];
-    GMP_CUDA(cudaStreamWaitEvent(t, c->events[2 * j], 0));
-    GMP_CUDA(cudaMemsetAsync(c->h_status + j, 0, sizeof(int32_t), t));
-    unsigned long long* counter = c->counter + 48 + k;
-    GMP_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), t));
-    uint8_t* dec_out = to_device ? static_cast<uint8_t*>(outs[q.file]) : c->h_out + F.out_off;
-    gmp_file_desc D{c->h_comp + F.comp_off, bytes[q.file], c->h_index + F.idx_off + q.b0, q.b1 - q.b0, dec_out,
-                    F.info.orig_size};
-    gmp::LaunchShape shape = c->shape;
-    shape.grid = (int)std::min<uint64_t>((q.b1 - q.b0 + wpc - 1) / wpc, part_warps / wpc);
-    GMP_CUDA(gmp::launch_decode(shape, nullptr, nullptr, 0, &D, c->h_status + j, counter,
-                                c->scratch + k * part_warps * c->slot_bytes, c->slot_bytes, c->shadow_off,
-                                c->max_seq, c->max_out, c->stats, (int)c->opts.collect_stats, (int)c->opts.resolve,
-                                t));
-    GMP_CUDA(cudaEventRecord(c->events[2 * j + 1], t));
+    const uint64_t c1x = std::min<uint64_t>(bytes[q.file], (c1 + 127) & ~uint64_t(127));
+    ce = cudaMemcpyAsync(c->h_comp + F.comp_off + c0, src + c0, c1x - c0, cudaMemcpyHostToDevice, c->h2d);
+    if (ce != cudaSuccess) {
+      rc = cuda_fail(ce, "cudaMemcpyAsync (piece in)");
+      break;
+    }
+    const CUresult r = ops->write(c->h2d, (CUdeviceptr)(in_ready + j), gen, CU_STREAM_WRITE_VALUE_DEFAULT);
+    if (r != CUDA_SUCCESS) rc = cu_fail(r, "cuStreamWriteValue32");
   }
-  // ... then the copies back, each after its piece's launch, on one copy
-  // stream per partition so that copies of pieces ending together overlap
-  for (size_t j = 0; j < n_pieces; j++) {
+  // ---- the copies back, each after its piece's flag (only once every copy
+  // in is queued, so no copy in waits behind them)
+  for (size_t j = 0; j < n_pieces && rc == GMP_OK && !to_device; j++) {
     const Piece& q = pieces[j];
     const File& F = files[q.file];
     const uint64_t o0 = F.idx[q.b0].out_offset;
     const uint64_t o1 = F.idx[q.b1 - 1].out_offset + F.idx[q.b1 - 1].out_bytes;
-    cudaStream_t u = c->d2h[j % parts];
-    GMP_CUDA(cudaStreamWaitEvent(u, c->events[2 * j + 1], 0));
-    if (o1 > o0 && !to_device)
-      GMP_CUDA(cudaMemcpyAsync(static_cast<uint8_t*>(host_outs[q.file]) + o0, c->h_out + F.out_off + o0, o1 - o0,
-                               cudaMemcpyDeviceToHost, u));
+    cudaStream_t u = c->d2h[j % gmp::kPipeParts];
+    const CUresult r = ops->wait(u, (CUdeviceptr)(out_ready + j), gen, CU_STREAM_WAIT_VALUE_GEQ);
+    if (r != CUDA_SUCCESS) {
+      rc = cu_fail(r, "cuStreamWaitValue32");
+      break;
+    }
+    if (o1 > o0) {
+      ce = cudaMemcpyAsync(static_cast<uint8_t*>(host_outs[q.file]) + o0, c->h_out + F.out_off + o0, o1 - o0,
+                           cudaMemcpyDeviceToHost, u);
+      if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaMemcpyAsync (piece back)");
+    }
   }
-  // every copy back has ended before the statuses are read
-  for (uint64_t k = 1; k < parts; k++) {
-    GMP_CUDA(cudaEventRecord(e_end, c->d2h[k]));
-    GMP_CUDA(cudaStreamWaitEvent(c->d2h[0], e_end, 0));
+  // ---- join: the launch, the copies in and every copy back end before the
+  // statuses are read
+  auto join = [&](cudaStream_t from) {
+    cudaError_t e = cudaEventRecord(c->ev[1], from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->d2h[0], c->ev[1], 0);
+    return e;
+  };
+  ce = join(c->pipe);
+  if (ce == cudaSuccess) ce = join(c->h2d);
+  for (uint32_t k = 1; k < gmp::kPipeParts && ce == cudaSuccess; k++) ce = join(c->d2h[k]);
+  std::vector<int32_t> st(n_pieces, 0);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(st.data(), c->h_status, n_pieces * sizeof(int32_t), cudaMemcpyDeviceToHost, c->d2h[0]);
+  const cudaError_t ce2 = cudaStreamSynchronize(c->d2h[0]);
+  if (ce == cudaSuccess) ce = ce2;
+  if (ce != cudaSuccess) {
+    // the joins could not be queued: wait for everything of this call
+    cudaStreamSynchronize(c->pipe);
+    cudaStreamSynchronize(c->h2d);
+    for (cudaStream_t t : c->d2h) cudaStreamSynchronize(t);
+    return rc ? rc : cuda_fail(ce, "host pipeline join");
   }
-  std::vector<int32_t> st(std::max<size_t>(n_pieces, 1), 0);
-  if (n_pieces)
-    GMP_CUDA(cudaMemcpyAsync(st.data(), c->h_status, n_pieces * sizeof(int32_t), cudaMemcpyDeviceToHost, c->d2h[0]));
-  GMP_CUDA(cudaStreamSynchronize(c->d2h[0]));
+  if (rc) return rc;
   // the caller's stream: ordered after this call's work
-  GMP_CUDA(cudaEventRecord(e_end, c->d2h[0]));
-  GMP_CUDA(cudaStreamWaitEvent(s, e_end, 0));
-  for (size_t f = 0; f < n_files; f++) statuses[f] = 0;
+  GMP_CUDA(cudaEventRecord(c->ev[1], c->d2h[0]));
+  GMP_CUDA(cudaStreamWaitEvent(s, c->ev[1], 0));
   for (size_t j = 0; j < n_pieces; j++)
     if (st[j] && !statuses[pieces[j].file]) statuses[pieces[j].file] = st[j];
   return GMP_OK;

@@ -26,11 +26,25 @@ constexpr int kWideWarpsPerSm = 16;
 size_t warp_smem_bytes(bool deep);
 cudaError_t configure_kernel(bool deep, size_t smem_bytes);
 cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, bool deep, int* ctas_per_sm);
+// Flags of a host-to-host launch (device arrays, one word per file of the
+// launch; see gmp_host.cpp): in_ready[f] reaches gen when file f's input has
+// been copied in (*abort_wait, zeroed before the launch, is set once a wait
+// runs out); the kernel sets out_ready[f] to gen when file f is decoded,
+// counting its blocks in done[f] and its exiting warps in *exited (both
+// zeroed before the launch).  in_ready and abort_wait alone may be given.
+struct PipeFlags {
+  const uint32_t* in_ready;
+  uint32_t* abort_wait;
+  uint32_t* out_ready;
+  uint32_t* done;
+  uint32_t* exited;
+  uint32_t gen;
+};
 cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, const uint64_t* item_start,
                           uint32_t n_files, const gmp_file_desc* single, int32_t* status,
                           unsigned long long* counter, uint8_t* scratch, uint64_t slot_bytes, uint64_t shadow_off,
                           uint32_t max_seq, uint32_t max_out, unsigned long long* stats, int collect_stats,
-                          int resolve, cudaStream_t stream, int spread = 1);
+                          int resolve, cudaStream_t stream, int spread = 1, const PipeFlags* pipe = nullptr);
 // compiled architecture of decode_kernel (cudaFuncGetAttributes)
 cudaError_t kernel_arch(int* binary_version, int* ptx_version);
 cudaError_t launch_batch_prefix(const gmp_file_desc* files, uint32_t n_files, uint64_t* item_start,
@@ -42,8 +56,8 @@ constexpr uint32_t kBlockFixed = 192;
 constexpr uint32_t kMaxSub = 64;
 constexpr uint32_t kLitLenSyms = 319;
 constexpr uint32_t kOffsetSyms = 30;
-// scratch partitions of the pipelined host-to-host calls (work counters
-// 48..63 of a context)
+// copy-back streams of the host-to-host calls (their launch uses work
+// counter 48 of a context)
 constexpr uint32_t kPipeParts = 8;
 
 // GPU compressor (gmp_gpucompress.cu) and its host half (gmp_compress.cpp):

@@ -1,8 +1,9 @@
 """GPU tests of the host-to-host calls (the paper's "(In/Out)" mode): streams
-in host memory, decoded by pipelined pieces, outputs back in host memory,
-byte for byte against the oracle, with pinned and pageable buffers, many
-pieces per partition, mixed formats, unaligned buffers, groups larger than
-the ring, and per-file error status."""
+in host memory, copied in piece by piece while one persistent launch decodes
+them, outputs copied back as pieces complete, byte for byte against the
+oracle, with pinned and pageable buffers, many pieces on a small launch,
+more pieces than the flag arrays first hold, mixed formats, unaligned
+buffers, groups larger than the ring, and per-file error status."""
 import numpy as np
 import pytest
 
@@ -69,10 +70,9 @@ def test_batch_of_mixed_streams_pinned_and_pageable(gmp):
     ctx.close()
 
 
-def test_many_pieces_per_partition(gmp):
-    # a small launch shape (152 warp slots, 8 partitions of 19) and 4 KiB
-    # blocks: each stream is cut into many one-wave pieces that queue on
-    # their partitions
+def test_many_pieces_small_launch(gmp):
+    # a small launch shape (152 warp slots) and 4 KiB blocks: 1538 blocks in
+    # 33 pieces of up to 49, each warp decoding blocks of many pieces
     streams, datas = [], []
     for i in range(3):
         data = datagen.csv_records(2 * MiB + 1000 * i, seed=70 + i)
@@ -84,6 +84,26 @@ def test_many_pieces_per_partition(gmp):
         assert sts == [0, 0, 0]
         for o, d in zip(outs, datas):
             assert np.array_equal(o, d)
+    ctx.close()
+
+
+def test_more_pieces_than_flags(gmp):
+    # 1100 small streams (one to three blocks, one piece each) are 1100
+    # pieces, more than the 1024 flag words a context first allocates; the
+    # next calls reuse the grown flags with fewer pieces, then more again
+    import torch
+    datas = [datagen.make_data("csv" if i % 2 else "text3", 3000 + 7 * i, 300 + i) for i in range(1100)]
+    streams = [gmp.compress(d, 4 * KiB, 4, 4 * KiB, de=(i % 3 == 0)) for i, d in enumerate(datas)]
+    ctx = gmp.Context(max_block_out=4 * KiB)
+    for sel in (slice(0, 1100), slice(0, 5), slice(17, 1100)):
+        outs, sts = ctx.decompress_host_batch(streams[sel])
+        assert sts == [0] * len(outs)
+        for o, d in zip(outs, datas[sel]):
+            assert np.array_equal(o, d)
+        douts, sts = ctx.decompress_from_host_batch(streams[sel])
+        assert sts == [0] * len(douts)
+        got = torch.cat([o for o in douts]).cpu().numpy()
+        assert np.array_equal(got, np.concatenate(datas[sel]))
     ctx.close()
 
 
@@ -161,7 +181,7 @@ def test_from_host_to_device_outputs(gmp):
     datas = [datagen.make_data("csv" if i % 2 else "text3", 500_000 + 77_777 * i, 60 + i) for i in range(5)]
     streams = [gmp.compress(d, 128 * KiB, 32, 32 * KiB, de=(i % 2 == 0), byte_mode=(i == 3))
                for i, d in enumerate(datas)]
-    for shape in ((0, 0), (1, 1)):  # default shape, and many pieces per partition
+    for shape in ((0, 0), (1, 1)):  # default shape, and a launch of 152 warps
         ctx = gmp.Context(max_block_out=128 * KiB, warps_per_cta=shape[0], ctas_per_sm=shape[1])
         for pinned in (False, True):
             ins = [_pin_copy(torch, s) for s in streams] if pinned else streams
