@@ -443,8 +443,7 @@ void gmp_server_destroy(gmp_server* s);
    Set-up: the array's device address belongs to one CUDA context.  The
    first call in each context (on each device, and again after a
    cudaDeviceReset) looks it up with cudaGetSymbolAddress, which loads the
-   module on that device; later calls in that context reuse it.  Make that
-   first call before any stream capture.
+   module on that device; later calls in that context reuse it.
    Every call shares the one array and clears its work counter: calls whose
    work overlaps on the GPU (different streams, or several host threads)
    race and must be serialised by the caller.
