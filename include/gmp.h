@@ -259,6 +259,16 @@ void gmp_context_destroy(gmp_context* ctx);
 int gmp_context_set_launch(gmp_context* ctx, uint32_t warps_per_cta, uint32_t ctas_per_sm);
 /* Bytes of device scratch the context holds. */
 size_t gmp_context_scratch_bytes(const gmp_context* ctx);
+/* Host-to-host calls: how long a warp waits for a piece's input copy before
+   the piece's file gets GMP_STATUS_INPUT_TIMEOUT (ms; 0 = the default,
+   10 000).  A longer limit suits slow pageable copies. */
+int gmp_context_set_input_wait(gmp_context* ctx, uint32_t ms);
+/* Test hook (fault injection on the host): the context's next host-to-host
+   call copies piece `piece` (0-based, in the call's piece order) in but does
+   not write its flag, so the warps waiting for it run out their wait and the
+   files of the call report GMP_STATUS_INPUT_TIMEOUT; -1 clears it.  The
+   kernel ends by itself, and the context stays usable. */
+int gmp_context_debug_drop_input_flag(gmp_context* ctx, int64_t piece);
 
 /* ------------------------------------------------------------------------ */
 /* Decompression of one stream (Sec. 3.2): one persistent launch, a warp per

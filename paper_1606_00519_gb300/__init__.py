@@ -228,6 +228,16 @@ class Context:
     def set_launch(self, warps_per_cta: int, ctas_per_sm: int = 0):
         _check(self._L.gmp_context_set_launch(self._h, warps_per_cta, ctas_per_sm), "gmp_context_set_launch")
 
+    def set_input_wait(self, ms: int):
+        """Host-to-host calls: a warp's wait limit for a piece's input (ms;
+        0 = the default 10 s)."""
+        _check(self._L.gmp_context_set_input_wait(self._h, ms), "gmp_context_set_input_wait")
+
+    def debug_drop_input_flag(self, piece: int):
+        """Test hook: the next host-to-host call does not flag piece
+        `piece`'s input (its waits run out; -1 clears)."""
+        _check(self._L.gmp_context_debug_drop_input_flag(self._h, piece), "gmp_context_debug_drop_input_flag")
+
     def scratch_bytes(self) -> int:
         return int(self._L.gmp_context_scratch_bytes(self._h))
 

@@ -158,6 +158,8 @@ def _declare(L):
     L.gmp_context_destroy.argtypes = [vp]
     L.gmp_context_destroy.restype = None
     L.gmp_context_set_launch.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
+    L.gmp_context_set_input_wait.argtypes = [vp, ctypes.c_uint32]
+    L.gmp_context_debug_drop_input_flag.argtypes = [vp, ctypes.c_int64]
     L.gmp_context_scratch_bytes.argtypes = [vp]
     L.gmp_context_scratch_bytes.restype = sz
     L.gmp_decompress.argtypes = [vp, vp, sz, vp, sz, vp, sz, vp, vp]

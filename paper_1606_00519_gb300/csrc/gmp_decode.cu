@@ -157,6 +157,7 @@ struct KParams {
   // the warps) for every file.
   const uint32_t* in_ready;
   uint32_t* abort_wait;  // set once a wait has run out: later waits give up at once
+  unsigned long long wait_ns;
   uint32_t* out_ready;
   uint32_t* done;
   uint32_t* exited;
@@ -175,11 +176,10 @@ __device__ __forceinline__ void st_global_32B(void* p, const uint4& a, const uin
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
 // ---- host-to-host pipeline flags
-// The wait for a file's input is bounded: about 10 s of the global timer, and
-// at most 2^24 polls; past that the file gets GMP_STATUS_INPUT_TIMEOUT, its
-// blocks are skipped and every later wait of the launch gives up at once, so
-// the launch always ends.
-constexpr unsigned long long kInputWaitNs = 10000000000ull;
+// The wait for a file's input is bounded: the host's limit (10 s unless the
+// context sets another) of the global timer, and at most 2^24 polls; past
+// that the file gets GMP_STATUS_INPUT_TIMEOUT, its blocks are skipped and
+// every later wait of the launch gives up at once, so the launch always ends.
 constexpr uint32_t kInputWaitPolls = 1u << 24;
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -201,7 +201,8 @@ __device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
 // and sleeps as one: with lane 0 polling and sleeping alone while the other
 // lanes waited at a shuffle, the warps decoded their next blocks 2 to 2.7
 // times slower (measured on text256m, (In) mode).
-__device__ __noinline__ bool wait_input(const uint32_t* flag, uint32_t* abort_wait, uint32_t gen) {
+__device__ __noinline__ bool wait_input(const uint32_t* flag, uint32_t* abort_wait, uint32_t gen,
+                                        unsigned long long wait_ns) {
   const unsigned long long t0 = global_ns();
   bool ok = false;
   for (uint32_t i = 0; i < kInputWaitPolls; i++) {
@@ -210,7 +211,7 @@ __device__ __noinline__ bool wait_input(const uint32_t* flag, uint32_t* abort_wa
     uint32_t v = 0, stop = 0;
     if ((threadIdx.x & 31u) == 0) {
       v = ld_acquire_sys(flag);
-      stop = *reinterpret_cast<volatile uint32_t*>(abort_wait) != 0u || global_ns() - t0 > kInputWaitNs;
+      stop = *reinterpret_cast<volatile uint32_t*>(abort_wait) != 0u || global_ns() - t0 > wait_ns;
     }
     v = __shfl_sync(0xffffffffu, v, 0);
     stop = __shfl_sync(0xffffffffu, stop, 0);
@@ -1392,7 +1393,7 @@ __global__ void __launch_bounds__(DEEP ? 128 : 512, DEEP ? 5 : 1) decode_kernel(
     } else {
       F = P.single;
     }
-    if (!kPipe || !P.in_ready || wait_input(P.in_ready + file, P.abort_wait, P.gen)) {
+    if (!kPipe || !P.in_ready || wait_input(P.in_ready + file, P.abort_wait, P.gen, P.wait_ns)) {
       decode_block<STATS, LLB>(S, P, F, b, P.status + file, slot, st_acc);
     } else if (lane == 0) {
       set_status(P.status + file, GMP_STATUS_INPUT_TIMEOUT);
@@ -1512,6 +1513,7 @@ cudaError_t launch_decode(const LaunchShape& shape, const gmp_file_desc* files, 
   P.spread = spread;
   P.in_ready = pipe ? pipe->in_ready : nullptr;
   P.abort_wait = pipe ? pipe->abort_wait : nullptr;
+  P.wait_ns = pipe ? pipe->wait_ns : 0ull;
   P.out_ready = pipe ? pipe->out_ready : nullptr;
   P.done = pipe ? pipe->done : nullptr;
   P.exited = pipe ? pipe->exited : nullptr;

@@ -112,6 +112,8 @@ struct gmp_context {
   uint32_t* h_flags = nullptr;
   size_t h_flags_n = 0;
   uint32_t pipe_gen = 0;
+  unsigned long long input_wait_ns = 10000000000ull;  // the kernel's limit per wait for a piece
+  int64_t drop_flag = -1;  // test hook: the next host call does not flag this piece's input
   // streams of the host-to-host calls: the launch, the copies in, the copies
   // back (several, so that a piece whose copy waits does not hold up the
   // others), and events between them
@@ -307,6 +309,18 @@ void gmp_context_destroy(gmp_context* c) {
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
   delete c;
+}
+
+int gmp_context_set_input_wait(gmp_context* c, uint32_t ms) {
+  if (!c) return GMP_ERR_INVALID_ARG;
+  c->input_wait_ns = (ms ? (unsigned long long)ms : 10000ull) * 1000000ull;
+  return GMP_OK;
+}
+
+int gmp_context_debug_drop_input_flag(gmp_context* c, int64_t piece) {
+  if (!c || piece < -1) return GMP_ERR_INVALID_ARG;
+  c->drop_flag = piece;
+  return GMP_OK;
 }
 
 int gmp_context_set_launch(gmp_context* c, uint32_t warps_per_cta, uint32_t ctas_per_sm) {
@@ -675,21 +689,13 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
   GMP_CUDA(cudaMemsetAsync(done, 0, (fn + 2) * sizeof(uint32_t), s));
   GMP_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
   GMP_CUDA(cudaEventRecord(c->ev[0], s));
-  // ---- the launch first: the copy streams' waits below are then queued
-  // after it, so it never waits behind them
-  GMP_CUDA(cudaStreamWaitEvent(c->pipe, c->ev[0], 0));
-  const gmp::PipeFlags pf{in_ready, done + fn + 1, to_device ? nullptr : out_ready, to_device ? nullptr : done,
-                          to_device ? nullptr : done + fn, gen};
-  GMP_CUDA(gmp::launch_decode(c->shape, reinterpret_cast<const gmp_file_desc*>(c->h_meta + desc_off),
-                              reinterpret_cast<const uint64_t*>(c->h_meta + pre_off), (uint32_t)n_pieces, nullptr,
-                              c->h_status, counter, c->scratch, c->slot_bytes, c->shadow_off, c->max_seq, c->max_out,
-                              c->stats, (int)c->opts.collect_stats, (int)c->opts.resolve, c->pipe, 1, &pf));
-  // From here on the launch runs: a failure below still waits for it (its
-  // waits for missing pieces end by themselves) before returning.
+  // ---- the copies in, in piece order, each followed by its piece's flag.
+  // They are queued before the launch: they wait on nothing, and a launch
+  // that blocks the host (CUDA_LAUNCH_BLOCKING, or a profiler replaying the
+  // kernel alone) then still finds its input arriving.
   rc = GMP_OK;
   cudaError_t ce = cudaStreamWaitEvent(c->h2d, c->ev[0], 0);
-  if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaStreamWaitEvent");
-  // ---- the copies in, in piece order, each followed by its piece's flag
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamWaitEvent");
   for (size_t j = 0; j < n_pieces && rc == GMP_OK; j++) {
     const Piece& q = pieces[j];
     const File& F = files[q.file];
@@ -702,11 +708,39 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
       rc = cuda_fail(ce, "cudaMemcpyAsync (piece in)");
       break;
     }
+    if ((int64_t)j == c->drop_flag) continue;  // the test hook's dropped flag
     const CUresult r = ops->write(c->h2d, (CUdeviceptr)(in_ready + j), gen, CU_STREAM_WRITE_VALUE_DEFAULT);
     if (r != CUDA_SUCCESS) rc = cu_fail(r, "cuStreamWriteValue32");
   }
-  // ---- the copies back, each after its piece's flag (only once every copy
-  // in is queued, so no copy in waits behind them)
+  c->drop_flag = -1;
+  // ---- the launch, before any copy-back wait is queued, so that it never
+  // waits behind one (streams may share a hardware queue)
+  if (rc == GMP_OK) {
+    ce = cudaStreamWaitEvent(c->pipe, c->ev[0], 0);
+    if (ce == cudaSuccess) {
+      const gmp::PipeFlags pf{in_ready,
+                              done + fn + 1,
+                              c->input_wait_ns,
+                              to_device ? nullptr : out_ready,
+                              to_device ? nullptr : done,
+                              to_device ? nullptr : done + fn,
+                              gen};
+      ce = gmp::launch_decode(c->shape, reinterpret_cast<const gmp_file_desc*>(c->h_meta + desc_off),
+                              reinterpret_cast<const uint64_t*>(c->h_meta + pre_off), (uint32_t)n_pieces, nullptr,
+                              c->h_status, counter, c->scratch, c->slot_bytes, c->shadow_off, c->max_seq, c->max_out,
+                              c->stats, (int)c->opts.collect_stats, (int)c->opts.resolve, c->pipe, 1, &pf);
+    }
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "decode launch (host pipeline)");
+  }
+  if (rc) {
+    // no launch, or no complete input: wait for the copies queued so far
+    // (and a launch whose waits for missing pieces end by themselves)
+    cudaStreamSynchronize(c->h2d);
+    cudaStreamSynchronize(c->pipe);
+    return rc;
+  }
+  // ---- the copies back, each after its piece's flag (queued last, so no
+  // copy in and not the launch waits behind them)
   for (size_t j = 0; j < n_pieces && rc == GMP_OK && !to_device; j++) {
     const Piece& q = pieces[j];
     const File& F = files[q.file];

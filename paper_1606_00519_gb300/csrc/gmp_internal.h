@@ -32,9 +32,11 @@ cudaError_t occupancy(int warps_per_cta, size_t smem_bytes, bool deep, int* ctas
 // runs out); the kernel sets out_ready[f] to gen when file f is decoded,
 // counting its blocks in done[f] and its exiting warps in *exited (both
 // zeroed before the launch).  in_ready and abort_wait alone may be given.
+// A wait for in_ready gives up after wait_ns of the GPU's global timer.
 struct PipeFlags {
   const uint32_t* in_ready;
   uint32_t* abort_wait;
+  unsigned long long wait_ns;
   uint32_t* out_ready;
   uint32_t* done;
   uint32_t* exited;

@@ -3,7 +3,10 @@ in host memory, copied in piece by piece while one persistent launch decodes
 them, outputs copied back as pieces complete, byte for byte against the
 oracle, with pinned and pageable buffers, many pieces on a small launch,
 more pieces than the flag arrays first hold, mixed formats, unaligned
-buffers, groups larger than the ring, and per-file error status."""
+buffers, groups larger than the ring, per-file error status, and a wait for
+input that runs out (a flag dropped on the host)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -201,4 +204,28 @@ def test_from_host_to_device_outputs(gmp):
     small = torch.empty(datas[1].size - 1, dtype=torch.uint8, device="cuda")
     with pytest.raises(gmp.GmpError):
         ctx.decompress_from_host_batch([streams[1]], [small])
+    ctx.close()
+
+
+def test_input_wait_runs_out(gmp):
+    # fault injected on the host: piece 0's input is copied but its flag is
+    # never written.  The warps waiting for it give up after the context's
+    # limit (200 ms), its file reports INPUT_TIMEOUT, the other file decodes,
+    # the kernel ends by itself, and the next call on the context is exact.
+    datas = [datagen.make_data("csv", 3_000_000, 401), datagen.make_data("text3", 2_000_000, 402)]
+    streams = [gmp.compress(d, 64 * KiB, 16, 32 * KiB) for d in datas]
+    ctx = gmp.Context(max_block_out=64 * KiB)
+    ctx.set_input_wait(200)
+    for call in (ctx.decompress_host_batch, ctx.decompress_from_host_batch):
+        ctx.debug_drop_input_flag(0)
+        t0 = time.perf_counter()
+        outs, sts = call(streams)
+        assert time.perf_counter() - t0 < 5.0
+        assert gmp.STATUS_NAMES[sts[0]] == "INPUT_TIMEOUT" and sts[1] == 0
+        got = outs[1] if isinstance(outs[1], np.ndarray) else outs[1].cpu().numpy()
+        assert np.array_equal(got, datas[1])
+        outs, sts = call(streams)  # no flag dropped: the context is still usable
+        assert sts == [0, 0]
+        for o, d in zip(outs, datas):
+            assert np.array_equal(o if isinstance(o, np.ndarray) else o.cpu().numpy(), d)
     ctx.close()
