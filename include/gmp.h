@@ -401,8 +401,9 @@ int gmp_decompress_from_host_batch(gmp_context* ctx, size_t n_files, const void*
 typedef struct gmp_server gmp_server;
 typedef struct {
   uint64_t budget_bytes;  /* device arena for request buffers (default 32 GiB) */
-  uint32_t n_lanes;       /* batches in flight at once (default 4) */
-  uint32_t max_batch;     /* requests per launch (default 256; 1 = one launch per request) */
+  uint32_t n_lanes;       /* batches in flight at once (default 8); each lane is a context with
+                             its own scratch (about 1.7 MB per resident warp for 256 KiB blocks) */
+  uint32_t max_batch;     /* requests per launch (default 64; 1 = one launch per request) */
   uint32_t max_block_out; /* largest block output of any request (default 256 KiB) */
   uint32_t warps_per_cta; /* launch shape of the lanes' contexts (0 = default) */
 } gmp_server_opts;

@@ -383,8 +383,8 @@ class Server:
     released.  poll() returns completions as dicts with the request id,
     status, output size and the submit / launch / done timestamps."""
 
-    def __init__(self, device: int | None = None, budget_bytes: int = 32 << 30, n_lanes: int = 4,
-                 max_batch: int = 256, max_block_out: int = 256 << 10, warps_per_cta: int = 0):
+    def __init__(self, device: int | None = None, budget_bytes: int = 32 << 30, n_lanes: int = 8,
+                 max_batch: int = 64, max_block_out: int = 256 << 10, warps_per_cta: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the server decodes only on the GPU")
