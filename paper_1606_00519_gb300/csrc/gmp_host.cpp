@@ -551,6 +551,8 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
   if (!c || (n_files && (!host_streams || !bytes || !host_outs || !out_caps || !statuses))) return GMP_ERR_INVALID_ARG;
   DeviceGuard guard(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t drop_flag = c->drop_flag;  // the test hook applies to this call only
+  c->drop_flag = -1;
   const StreamValueOps* ops = stream_value_ops();
   if (!ops) return cuda_fail(cudaErrorNotSupported, "cuStreamWriteValue32 / cuStreamWaitValue32 entry points");
   // ---- parse every stream; lay out the device staging
@@ -708,11 +710,10 @@ static int decompress_from_host(gmp_context* c, size_t n_files, const void* cons
       rc = cuda_fail(ce, "cudaMemcpyAsync (piece in)");
       break;
     }
-    if ((int64_t)j == c->drop_flag) continue;  // the test hook's dropped flag
+    if ((int64_t)j == drop_flag) continue;  // the test hook's dropped flag
     const CUresult r = ops->write(c->h2d, (CUdeviceptr)(in_ready + j), gen, CU_STREAM_WRITE_VALUE_DEFAULT);
     if (r != CUDA_SUCCESS) rc = cu_fail(r, "cuStreamWriteValue32");
   }
-  c->drop_flag = -1;
   // ---- the launch, before any copy-back wait is queued, so that it never
   // waits behind one (streams may share a hardware queue)
   if (rc == GMP_OK) {
