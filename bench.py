@@ -828,9 +828,9 @@ def run_compress(args):
 
 def _concurrency(spans):
     """Batched launches in flight at once, from each distinct launch's
-    (launch time, completion time) on the host clock (requests of one batch
-    share their launch): the largest count over time and the time-weighted
-    mean while any launch is in flight."""
+    (start, end) on one clock (requests of one batch share their launch):
+    the largest count over time and the time-weighted mean while any launch
+    is in flight."""
     ev = sorted([(a, 1) for a, b in spans] + [(b, -1) for a, b in spans])
     cur = peak = 0
     busy = area = 0.0
@@ -872,7 +872,7 @@ def serve_result(args):
         total bytes, wall seconds; checks every output's size and status, and
         after the run the bytes of a sample (every 97th request)."""
         lat, done, nbytes = [], 0, 0
-        spans = set()
+        spans, gpu_spans = set(), set()
         ids = {}
         errors = []
         checked = []  # sampled requests whose bytes are compared after the run
@@ -888,6 +888,7 @@ def serve_result(args):
                         errors.append((i, c["status"]))
                     lat.append(c["t_done"] - c["t_submit"])
                     spans.add((c["t_start"], c["t_done"]))
+                    gpu_spans.add((c["t_gpu_ready"], c["t_gpu_done"]))
                     nbytes += c["out_bytes"]
                     if i % 97 == 0:
                         checked.append((i, c["id"], c["out_bytes"]))  # kept on the device until then
@@ -917,6 +918,7 @@ def serve_result(args):
         if errors:
             raise SystemExit(f"serve: {len(errors)} bad results, e.g. {errors[:3]}")
         run.last_concurrency = _concurrency(spans)
+        run.last_gpu_concurrency = _concurrency(gpu_spans)
         return np.array(lat), nbytes, wall
 
     n = args.serve_requests
@@ -938,7 +940,10 @@ def serve_result(args):
         run(srv, np.zeros(n), picks)
         lat, nb, wall = run(srv, np.zeros(n), picks)
         peak = nb / wall / 1e9
-        out = {"peak_gbs": round(peak, 3), "peak_launches_in_flight": run.last_concurrency}
+        # launches in flight on the host clock (launch -> completion seen), and
+        # decodes on the GPU's clock (inputs in and decode next -> decode end)
+        out = {"peak_gbs": round(peak, 3), "peak_launches_in_flight": run.last_concurrency,
+               "peak_decodes_on_gpu": run.last_gpu_concurrency}
         for load in (0.25, 0.5, 0.9):
             rate = load * peak * 1e9 / mean_size
             arr = datagen.poisson_arrivals(seed=int(load * 100), n=n, rate_per_s=rate)
@@ -947,7 +952,8 @@ def serve_result(args):
                                               "served_gbs": round(nb / wall / 1e9, 3),
                                               "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                                               "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
-                                              "launches_in_flight": run.last_concurrency}
+                                              "launches_in_flight": run.last_concurrency,
+                                              "decodes_on_gpu": run.last_gpu_concurrency}
         srv.close()
         result[name] = out
     result["value"] = result["batched"]["peak_gbs"]

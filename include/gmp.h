@@ -412,7 +412,12 @@ typedef struct {
   int32_t status;        /* gmp_status of the decode */
   uint8_t* d_out;        /* device output, valid until gmp_server_release(id) */
   uint64_t out_bytes;
-  double t_submit, t_start, t_done;
+  double t_submit, t_start, t_done;  /* host clock (s): submitted, its batch launched, batch done */
+  /* device clock (s, CUDA events on the lane's stream, from the server's
+     creation): its batch's inputs copied in and the decode next on the
+     stream, and the decode ended.  Batches whose intervals overlap ran on
+     the GPU at the same time. */
+  double t_gpu_ready, t_gpu_done;
 } gmp_completion;
 
 void gmp_server_opts_default(gmp_server_opts* o);

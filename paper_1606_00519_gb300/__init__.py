@@ -408,7 +408,8 @@ class Server:
         n = ctypes.c_size_t()
         _check(self._L.gmp_server_poll(self._h, buf, max_n, ctypes.byref(n), wait_ms), "gmp_server_poll")
         return [{"id": buf[i].id, "status": buf[i].status, "out_bytes": buf[i].out_bytes,
-                 "t_submit": buf[i].t_submit, "t_start": buf[i].t_start, "t_done": buf[i].t_done}
+                 "t_submit": buf[i].t_submit, "t_start": buf[i].t_start, "t_done": buf[i].t_done,
+                 "t_gpu_ready": buf[i].t_gpu_ready, "t_gpu_done": buf[i].t_gpu_done}
                 for i in range(n.value)]
 
     def copy_out(self, rid: int, dst) -> None:

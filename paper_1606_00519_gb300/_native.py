@@ -117,7 +117,7 @@ class ServerOpts(ctypes.Structure):
 class Completion(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("d_out", ctypes.c_uint64),
                 ("out_bytes", ctypes.c_uint64), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("t_gpu_ready", ctypes.c_double), ("t_gpu_done", ctypes.c_double)]
 
 
 class GpuCompressTimes(ctypes.Structure):

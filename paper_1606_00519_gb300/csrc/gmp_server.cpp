@@ -111,6 +111,8 @@ struct Lane {
   std::atomic<bool> done{false};
   double t_done = 0;
   bool busy = false;
+  // the batch's decode: next on the stream (inputs copied in), and ended
+  cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
 };
 
 }  // namespace
@@ -130,6 +132,7 @@ struct gmp_server {
   int error = 0;
   bool stop = false;
   Clock::time_point t0 = Clock::now();
+  cudaEvent_t base = nullptr;  // device-clock origin of the completions' device times
   std::thread sched;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -173,8 +176,10 @@ int gmp_server::launch(Lane& L, std::vector<std::shared_ptr<Request>>& reqs) {
   if (cudaMemcpyAsync(L.d_table, L.h_table, n * sizeof(gmp_file_desc), cudaMemcpyHostToDevice, L.stream) !=
       cudaSuccess)
     return GMP_ERR_CUDA;
+  if (cudaEventRecord(L.ev_ready, L.stream) != cudaSuccess) return GMP_ERR_CUDA;
   int rc = gmp_decompress_batch(L.ctx, L.d_table, n, L.d_status, L.stream);
   if (rc) return rc;
+  if (cudaEventRecord(L.ev_done, L.stream) != cudaSuccess) return GMP_ERR_CUDA;
   if (cudaMemcpyAsync(L.h_status, L.d_status, n * sizeof(int32_t), cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
     return GMP_ERR_CUDA;
   L.batch = reqs;
@@ -197,6 +202,11 @@ void gmp_server::loop() {
     for (auto& Lp : lanes) {
       Lane& L = *Lp;
       if (L.busy && L.done.load(std::memory_order_acquire)) {
+        // device times of the batch (both events completed before the
+        // lane's completion function ran)
+        float ms_ready = 0.f, ms_done = 0.f;
+        cudaEventElapsedTime(&ms_ready, base, L.ev_ready);
+        cudaEventElapsedTime(&ms_done, base, L.ev_done);
         for (size_t i = 0; i < L.batch.size(); i++) {
           Request& r = *L.batch[i];
           r.status = L.h_status[i];
@@ -209,6 +219,8 @@ void gmp_server::loop() {
           c.t_submit = r.t_submit;
           c.t_start = r.t_start;
           c.t_done = r.t_done;
+          c.t_gpu_ready = ms_ready * 1e-3;
+          c.t_gpu_done = ms_done * 1e-3;
           completed.push_back(c);
           in_system--;
         }
@@ -313,10 +325,15 @@ int gmp_server_create(gmp_server** out, int device, const gmp_server_opts* opts)
         cudaMallocHost(&L->h_table, o.max_batch * sizeof(gmp_file_desc)) != cudaSuccess ||
         cudaMalloc(&L->d_table, o.max_batch * sizeof(gmp_file_desc)) != cudaSuccess ||
         cudaMallocHost(&L->h_status, o.max_batch * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&L->d_status, o.max_batch * sizeof(int32_t)) != cudaSuccess)
+        cudaMalloc(&L->d_status, o.max_batch * sizeof(int32_t)) != cudaSuccess ||
+        cudaEventCreate(&L->ev_ready) != cudaSuccess || cudaEventCreate(&L->ev_done) != cudaSuccess)
       rc = GMP_ERR_CUDA;
     S->lanes.push_back(std::move(L));
   }
+  if (rc == GMP_OK &&
+      (cudaEventCreate(&S->base) != cudaSuccess || cudaEventRecord(S->base, S->lanes[0]->stream) != cudaSuccess ||
+       cudaEventSynchronize(S->base) != cudaSuccess))
+    rc = GMP_ERR_CUDA;
   cudaSetDevice(prev);
   if (rc) {
     gmp_server_destroy(S.release());
@@ -436,7 +453,10 @@ void gmp_server_destroy(gmp_server* S) {
     if (L.d_table) cudaFree(L.d_table);
     if (L.h_status) cudaFreeHost(L.h_status);
     if (L.d_status) cudaFree(L.d_status);
+    if (L.ev_ready) cudaEventDestroy(L.ev_ready);
+    if (L.ev_done) cudaEventDestroy(L.ev_done);
   }
+  if (S->base) cudaEventDestroy(S->base);
   delete S;
 }
 

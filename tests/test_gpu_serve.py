@@ -65,6 +65,7 @@ def test_serving_mixed_requests(gmp, requests):
         c, got = outs[i]
         assert c["status"] == 0
         assert c["t_submit"] <= c["t_start"] <= c["t_done"]
+        assert 0.0 <= c["t_gpu_ready"] <= c["t_gpu_done"]
         assert np.array_equal(got, data)
     assert srv.bytes_in_use() == 0
     srv.close()
@@ -116,9 +117,9 @@ def test_serving_shape_of_the_load_configuration(gmp):
     """The serving configuration's request shape: sizes log-uniform from
     16 KiB to 64 MiB, mixed content and modes, arriving while others run,
     under a budget that holds only some of them (2 GiB here instead of 32).
-    Several lanes must be busy at the same time (their batches' launch-to-
-    completion intervals overlap), and every output must equal the input and
-    the same request decoded alone (tolerance: 0 bytes)."""
+    Several lanes must be busy at the same time (their batches' intervals
+    overlap on the host's and on the GPU's clock), and every output must equal
+    the input and the same request decoded alone (tolerance: 0 bytes)."""
     mix = datagen.request_mix(seed=21, n=40, lo=16 * KiB, hi=64 * MiB)
     reqs = []
     for size, kind, mode, sd in mix:
@@ -128,17 +129,20 @@ def test_serving_shape_of_the_load_configuration(gmp):
     srv = gmp.Server(budget_bytes=2 << 30, n_lanes=4, max_batch=8)
     mixed = _run(gmp, srv, reqs, spacing_s=0.0005)
     assert len(mixed) == len(reqs)
-    spans = []
+    spans, gpu_spans = [], []
     for i, (data, _) in enumerate(reqs):
         c, got = mixed[i]
         assert c["status"] == 0 and np.array_equal(got, data)
         spans.append((c["t_start"], c["t_done"]))
+        gpu_spans.append((c["t_gpu_ready"], c["t_gpu_done"]))
     # distinct launches (requests of one batch share theirs) whose launch-to-
     # completion intervals overlap: batches of different lanes in flight at
-    # the same time
-    launches = sorted(set(spans))
-    overlaps = sum(1 for a, b in zip(launches, launches[1:]) if b[0] < a[1])
-    assert len(launches) >= 2 and overlaps >= 1
+    # the same time, on the host's clock and on the GPU's (from the inputs
+    # being in to the decode's end)
+    for sp in (spans, gpu_spans):
+        launches = sorted(set(sp))
+        overlaps = sum(1 for a, b in zip(launches, launches[1:]) if b[0] < a[1])
+        assert len(launches) >= 2 and overlaps >= 1
     # the largest requests again, alone
     for i in sorted(range(len(reqs)), key=lambda k: -reqs[k][0].size)[:4]:
         alone = _run(gmp, srv, [reqs[i]])
