@@ -560,7 +560,9 @@ def batch_result(args, cap):
     ONE persistent launch replayed from a CUDA graph, against one
     gmp_decompress launch per file on the same stream.  Block size and
     sub-blocks per block come from the format autotuner on a sample of the
-    mix.  Returns the figures as a dict."""
+    mix, the launch shape from the launch autotuner on the whole batch; with
+    --warps-per-cta (a profiling run) neither tuner runs: 256 KiB blocks of
+    32 sub-blocks and the given shape.  Returns the figures as a dict."""
     import torch
     import paper_1606_00519_gb300 as gmp
     from paper_1606_00519_gb300 import autotune
@@ -568,15 +570,19 @@ def batch_result(args, cap):
     mix = datagen.file_mix(seed=4, n_files=args.batch_files, lo=4 * KiB, hi=16 * MiB, total_cap=cap)
     # a sample large enough to fill the GPU (the tuner times throughput, not
     # the latency of a small input): the first files of the mix, 128 MiB
-    parts, got = [], 0
-    for sz, kind, mode, sd in mix:
-        if got >= 128 * MiB:
-            break
-        parts.append(datagen.make_data(kind, sz, sd))
-        got += sz
-    sample = np.concatenate(parts)
+    fixed = args.warps_per_cta > 0
     t0 = time.perf_counter()
-    tuned = autotune.tune(sample, block_sizes=(128 * KiB, 256 * KiB), n_subs=(32, 64), repeats=3)
+    if fixed:
+        tuned = {"fixed": True, "block_size": 256 * KiB, "n_sub": 32}
+    else:
+        parts, got = [], 0
+        for sz, kind, mode, sd in mix:
+            if got >= 128 * MiB:
+                break
+            parts.append(datagen.make_data(kind, sz, sd))
+            got += sz
+        sample = np.concatenate(parts)
+        tuned = autotune.tune(sample, block_sizes=(128 * KiB, 256 * KiB), n_subs=(32, 64), repeats=3)
     t_tune = time.perf_counter() - t0
     bs, k = tuned["block_size"], tuned["n_sub"]
     files, total, comp_total = [], 0, 0
@@ -594,7 +600,11 @@ def batch_result(args, cap):
     ctx = gmp.Context(max_block_out=bs, max_files=len(files))
     # the launch shape for the whole batch (the format tuner's shape was
     # chosen on its sample, a fraction of the batch's blocks)
-    shape = ctx.autotune(table, len(files), status)
+    if fixed:
+        ctx.set_launch(args.warps_per_cta, args.ctas_per_sm)
+        shape = {"warps_per_cta": args.warps_per_cta, "ctas_per_sm": args.ctas_per_sm}
+    else:
+        shape = ctx.autotune(table, len(files), status)
     graph = ctx.batch_graph(table, len(files), status)
     stream = torch.cuda.current_stream()
 
