@@ -252,7 +252,10 @@ typedef enum { GMP_RESOLVE_AUTO = 0, GMP_RESOLVE_MRR = 1, GMP_RESOLVE_SC = 2 } g
 void gmp_context_opts_default(gmp_context_opts* o);
 /* Creates a context on `device`: allocates the scratch of one persistent
    launch (one slot per resident warp) and a small device work counter.
-   opts may be NULL. */
+   opts may be NULL.  A context is not thread-safe, and its launches share
+   the scratch: calls on one context must not run at the same time, from
+   several host threads or on streams whose work overlaps (use a context per
+   stream, as the serving loop's lanes do). */
 int gmp_context_create(gmp_context** ctx, int device, const gmp_context_opts* opts);
 void gmp_context_destroy(gmp_context* ctx);
 /* Change launch shape (an autotuner result); reallocates scratch if needed. */
