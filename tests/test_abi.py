@@ -199,6 +199,8 @@ def test_entry_points_reject_null_arguments(lib):
     assert lib.gmp_decompress_from_host_batch(None, 1, None, None, None, None, None, None) == INVALID
     assert lib.gmp_decompress_host(None, None, 0, None, 0, None, None) == INVALID
     assert lib.gmp_stats_reset(None, None) == INVALID
+    assert lib.gmp_context_set_input_wait(None, ctypes.c_uint32(100)) == INVALID
+    assert lib.gmp_context_debug_drop_input_flag(None, ctypes.c_int64(0)) == INVALID
     assert lib.gmp_index_build(None, 0, None, 0, ctypes.byref(z), None) == INVALID
 
 
