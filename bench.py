@@ -411,6 +411,8 @@ def measure_decode(args, w, data, streams, dev, dist=None, rank=0, clocks=False,
                      "kernel": "gmp::decode_kernel (persistent; one launch per step)",
                      "algorithmic_bytes_per_launch": int(algo_bytes),
                      "launch_avg_ms": round(launch_avg_ms, 4),
+                     "launch_median_ms": round(float(np.median(per_launch)), 4),
+                     "launch_min_ms": round(float(np.min(per_launch)), 4),
                      "decompressed_frac_of_roofline": round(value / (hbm_peak * (out_bytes / algo_bytes)), 4)},
         "clocks": clk,
     }
