@@ -2,7 +2,7 @@
 in host memory, copied in piece by piece while one persistent launch decodes
 them, outputs copied back as pieces complete, byte for byte against the
 oracle, with pinned and pageable buffers, many pieces on a small launch,
-more pieces than the flag arrays first hold, mixed formats, unaligned
+1 MiB blocks, more pieces than the flag arrays first hold, mixed formats, unaligned
 buffers, groups larger than the ring, per-file error status, and a wait for
 input that runs out (a flag dropped on the host)."""
 import time
@@ -87,6 +87,23 @@ def test_many_pieces_small_launch(gmp):
         assert sts == [0, 0, 0]
         for o, d in zip(outs, datas):
             assert np.array_equal(o, d)
+    ctx.close()
+
+
+def test_large_blocks_both_modes(gmp):
+    # 1 MiB blocks of 64 sub-blocks (the Huffman phase takes them 32 at a
+    # time) through both host calls, MRR and DE, against the oracle
+    datas = [datagen.make_data("csv", 9 * MiB + 12345, 501), datagen.make_data("text3", 6 * MiB + 777, 502)]
+    streams = [gmp.compress(d, 1 * MiB, 64, 32 * KiB, de=(i == 1)) for i, d in enumerate(datas)]
+    ctx = gmp.Context(max_block_out=1 * MiB)
+    outs, sts = ctx.decompress_host_batch(streams)
+    assert sts == [0, 0]
+    for o, d, st in zip(outs, datas, streams):
+        assert np.array_equal(o, d) and np.array_equal(o, oracle.decompress(st))
+    douts, sts = ctx.decompress_from_host_batch(streams)
+    assert sts == [0, 0]
+    for o, d in zip(douts, datas):
+        assert np.array_equal(o.cpu().numpy(), d)
     ctx.close()
 
 
